@@ -1,0 +1,177 @@
+"""Pins of the oracle's lattice-Boltzmann part and colloid boundary (Sec. 2.2).
+
+Analytic Poiseuille flow between half-way bounce-back walls, exact mass and
+momentum conservation, zero force on a static colloid in a fluid at rest,
+Stokes drag on a periodic array (force balance and Hasimoto's correction),
+and a brute-force enumeration of the boundary links.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+@pytest.mark.parametrize("nz", [8, 16])
+def test_poiseuille_exact_at_magic_tau(nz):
+    """BGK + half-way bounce-back + Guo forcing: with (tau - 1/2)^2 = 3/16 the
+    steady profile is the parabola with no-slip walls exactly at z = -1/2 and
+    nz - 1/2:  u(z) = g/(2 nu) (z + 1/2)(nz - 1/2 - z), nu = (tau - 1/2)/3."""
+    tau, g = 0.5 + math.sqrt(3.0 / 16.0), 1e-6
+    o = oracle.Oracle(1, 1, nz, wall_z=True, tau=tau, lc=False, body_force=(g, 0, 0))
+    o.step(400 * nz * nz // 16 + 2000)
+    _, u = o.get_rho_u()
+    ux = u[0, :, 0, 0]
+    nu = (tau - 0.5) / 3
+    z = np.arange(nz)
+    ana = g / (2 * nu) * (z + 0.5) * (nz - 0.5 - z)
+    np.testing.assert_allclose(ux, ana, rtol=1e-9)
+    np.testing.assert_allclose(u[1:], 0.0, atol=1e-14)
+
+
+def test_poiseuille_curvature_tau25():
+    """At tau = 2.5 the profile's second difference is -g/nu exactly and the
+    profile is symmetric; the wall slip is tau-dependent (recorded)."""
+    tau, g, nz = 2.5, 1e-6, 16
+    o = oracle.Oracle(1, 1, nz, wall_z=True, tau=tau, lc=False, body_force=(g, 0, 0))
+    o.step(3000)
+    _, u = o.get_rho_u()
+    ux = u[0, :, 0, 0]
+    nu = (tau - 0.5) / 3
+    d2 = ux[2:] - 2 * ux[1:-1] + ux[:-2]
+    np.testing.assert_allclose(d2, -g / nu, rtol=1e-9)
+    np.testing.assert_allclose(ux, ux[::-1], rtol=1e-12)
+    ana = g / (2 * nu) * (np.arange(nz) + 0.5) * (nz - 0.5 - np.arange(nz))
+    slip = (ux - ana)[0]
+    assert 0 < slip / ana.max() < 0.2
+
+
+@pytest.mark.parametrize("lc", [False, True])
+def test_mass_conserved_with_static_colloid(lc):
+    L = 12
+    o = oracle.Oracle(L, L, L, **synth.NEMATIC, lc=lc, threads=4)
+    o.init_uniaxial((0, 0, 1), amp=1e-2, seed=3)
+    o.add_colloid((5.5, 5.5, 5.5), 3.0, oracle.PLANAR, w=0.01)
+    c, w = oracle.lattice()
+    sol = o.get_solid()
+    f = w[:, None, None, None] + synth.random_f_dev((L, L, L), seed=4, amp=1e-3)
+    f[:, sol >= 0] = 0.0
+    o.set_f(f)
+    m0 = o.diag()["mass"]
+    o.step(200)
+    m1 = o.diag()["mass"]
+    assert abs(m1 - m0) / m0 < 1e-13
+
+
+def test_momentum_conserved_fluid_plus_colloid():
+    """Sec. 2.2: the colloid LC force sums P over the solid-fluid faces so that
+    momentum lost by the fluid is gained by the colloid; bounce-back hands the
+    link momentum to the colloid.  Fluid momentum + colloid impulse is constant."""
+    L = 12
+    o = oracle.Oracle(L, L, L, **dict(synth.NEMATIC, A0=0.1, K=0.02), threads=4)
+    o.init_uniaxial((0.3, 0.1, 1.0), amp=5e-2, seed=8)
+    o.add_colloid((5.5, 6.0, 5.2), 3.1, oracle.PLANAR, w=0.05)
+    p0 = o.diag()["momentum"]
+    o.step(50)
+    d = o.diag()
+    c = o.colloid(0)
+    assert np.abs(c["impulse"]).max() > 1e-8  # something was exchanged
+    np.testing.assert_allclose(d["momentum"] + c["impulse"], p0, atol=1e-13)
+
+
+def test_static_colloid_quiescent_fluid_has_no_force():
+    L = 12
+    o = oracle.Oracle(L, L, L, **synth.NEMATIC, lc=False)
+    o.add_colloid((5.5, 5.5, 5.5), 3.3, oracle.NORMAL)
+    o.step(3)
+    c = o.colloid(0)
+    assert np.abs(c["F_hyd"]).max() < 1e-14
+    assert np.abs(c["T_hyd"]).max() < 1e-14
+
+
+@pytest.mark.slow
+def test_stokes_drag_periodic_array():
+    """Fixed sphere (a0 = 5 >= the resolution threshold of Fig. 1) in a periodic
+    L^3 box driven by a body force g: at steady state the drag equals g * N_fluid
+    (force balance), and matches Hasimoto's periodic-array drag
+    F = 6 pi eta a U / (1 - 2.837 a/L + 4.19 (a/L)^3 - 27.4 (a/L)^6),
+    U the mean velocity over the cell, within 1%."""
+    L, a0, g, tau = 24, 5.0, 1e-6, 1.0
+    o = oracle.Oracle(L, L, L, tau=tau, lc=False, body_force=(g, 0, 0), threads=8)
+    c = (L - 1) / 2
+    o.add_colloid((c, c, c), a0, oracle.NORMAL)
+    o.step(6000)
+    F = o.colloid(0)["F_hyd"]
+    nfl = o.diag()["n_fluid"]
+    assert abs(F[0] - g * nfl) / (g * nfl) < 5e-6
+    assert abs(F[1]) < 1e-12 and abs(F[2]) < 1e-12
+    _, u = o.get_rho_u()
+    U = u[0][o.get_solid() < 0].sum() / L**3
+    eta = (tau - 0.5) / 3
+    x = a0 / L
+    Fh = 6 * math.pi * eta * a0 * U / (1 - 2.837 * x + 4.19 * x**3 - 27.4 * x**6)
+    assert abs(F[0] / Fh - 1) < 0.01
+
+
+def _brute_links(L, X, a0):
+    nx, ny, nz = L
+    c, _ = oracle.lattice()
+
+    def mi(d, n):
+        if d >= 0.5 * n:
+            d -= n
+        elif d < -0.5 * n:
+            d += n
+        return d
+
+    def solid(x, y, z):
+        dx, dy, dz = mi(x - X[0], nx), mi(y - X[1], ny), mi(z - X[2], nz)
+        return dx * dx + dy * dy + dz * dz < a0 * a0
+
+    out = []
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                if solid(x, y, z):
+                    continue
+                for q in range(1, 19):
+                    if solid((x + c[q][0]) % nx, (y + c[q][1]) % ny, (z + c[q][2]) % nz):
+                        out.append((x + nx * (y + ny * z), q))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_links_match_brute_force(seed):
+    rng = np.random.default_rng(100 + seed)
+    L = tuple(int(v) for v in rng.integers(6, 13, size=3))
+    X, a0 = synth.random_colloid(L, seed=200 + seed)
+    o = oracle.Oracle(*L, lc=False)
+    o.add_colloid(X, a0, oracle.NORMAL)
+    node, d, col = o.links()
+    ref = _brute_links(L, X, a0)
+    assert len(ref) == len(node)
+    assert [(int(a), int(b)) for a, b in zip(node, d)] == ref
+    assert (col == 0).all()
+    sol = o.get_solid().reshape(-1)
+    for i in range(L[0] * L[1] * L[2]):
+        z, r = divmod(i, L[0] * L[1])
+        y, x = divmod(r, L[0])
+        dx = [x - X[0], y - X[1], z - X[2]]
+        for k, n in enumerate(L):
+            if dx[k] >= 0.5 * n:
+                dx[k] -= n
+            elif dx[k] < -0.5 * n:
+                dx[k] += n
+        assert (sol[i] == 0) == (dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2] < a0 * a0)
+
+
+def test_overlapping_colloids_rejected():
+    o = oracle.Oracle(16, 16, 16, lc=False)
+    o.add_colloid((4.0, 4.0, 4.0), 3.0)
+    with pytest.raises(ValueError):
+        o.add_colloid((6.0, 4.0, 4.0), 3.0)
+    o2 = oracle.Oracle(16, 16, 16, wall_z=True, lc=False)
+    with pytest.raises(ValueError):
+        o2.add_colloid((8.0, 8.0, 1.0), 3.0)
