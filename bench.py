@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Throughput of the coupled LB + Beris-Edwards step on GB300 (one JSON line).
+
+Default workload: the 128^3 periodic cholesteric (pitch 32 lattice units,
+helix start) with one R = 8 colloid of normal anchoring w = 0.02, FP32
+storage with FP64 reductions -- the largest single-GPU workload of the
+paper-shaped runs, and larger than L2.  A "step" is one full coupled step
+(LC stress + body force, LB collide/stream with bounce-back, Q update, link
+momentum exchange, colloid update), replayed from a captured CUDA graph.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With N > 1 (under torchrun) every rank advances its own box (replicas, weak
+scaling) and rank 0 prints the whole-job MLUPS with the max time over ranks.
+``--impl reference`` times the FP64 CPU oracle on the host cores (rank 0 only)
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS of coupled LB+Beris–Edwards step; time-to-relaxed-defect vs plain"
+LB_BYTES = 19 * 4 * 2          # algorithmic bytes per fluid node of the LB kernel (df read + write, FP32)
+STEP_BYTES = (19 + 5) * 4 * 2  # algorithmic bytes per node of the whole coupled step (df and Q, read + write)
+KERNEL_SOURCES = ("paper_1102_2193_gb300/csrc/lclb_kernels.cu", "paper_1102_2193_gb300/csrc/lclb_dev.cuh")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm=float(d["hbm_gbs"]), src="measured")
+    return dict(hbm=6800.0, src="fallback")
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch recorded by the committed ncu summary, if it was
+    taken on the current kernel source (its hash line matches)."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    if not os.path.exists(p):
+        return None
+    d = {}
+    with open(p) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                d[k.strip()] = v.strip()
+    if d.get("kernel_source_sha256_16") != kernel_hash():
+        return None
+    try:
+        return float(d["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=mx, reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+def setup_dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_box(P, w, stream, precision):
+    nx, ny, nz = w["grid"]
+    s = P.Solver(nx, ny, nz, wall_z=w["wall_z"], stream=stream, precision=precision, **w["params"])
+    ini = w["init"]
+    if ini["kind"] == "helix":
+        s.init_helix(ini["axis"], ini["amp"], ini["seed"])
+    else:
+        s.init_uniaxial(ini["n"], ini["amp"], ini["seed"])
+    for c in w["colloids"]:
+        s.add_colloid(c["X"], c["a0"], c["anchoring"], c["w"], c["mobile"], c.get("F_ext"))
+    return s
+
+
+def cpu_baseline(w, budget_s: float) -> dict:
+    """The FP64 oracle as it stands, on this host's cores, on a bounded number
+    of steps of the same workload."""
+    import oracle
+    cores = os.cpu_count() or 1
+    nx, ny, nz = w["grid"]
+    o = oracle.Oracle(nx, ny, nz, wall_z=w["wall_z"], threads=cores, **w["params"])
+    ini = w["init"]
+    if ini["kind"] == "helix":
+        o.init_helix(ini["axis"], ini["amp"], ini["seed"])
+    else:
+        o.init_uniaxial(ini["n"], ini["amp"], ini["seed"])
+    for c in w["colloids"]:
+        o.add_colloid(c["X"], c["a0"], c["anchoring"], c["w"], c["mobile"], c.get("F_ext"))
+    o.step(1)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        o.step(1)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s or n >= 1000:
+            break
+    return dict(value=nx * ny * nz * n / dt / 1e6, unit="MLUPS", cores=cores, kind="oracle",
+                sample=f"{n} steps of the {nx}x{ny}x{nz} workload after 1 untimed step, FP64, {cores} threads")
+
+
+def run_reference(args, ws, rank):
+    import synth
+    if rank != 0:
+        return 0
+    w = synth.workload(args.workload)
+    # bounded sample: the same physics on a 48^3 box with the colloid at its centre
+    L = 48
+    w = dict(w, grid=(L, L, L), colloids=[dict(c, X=((L - 1) / 2,) * 3) for c in w["colloids"]])
+    import oracle
+    cores = os.cpu_count() or 1
+    o = oracle.Oracle(L, L, L, wall_z=w["wall_z"], threads=cores, **w["params"])
+    ini = w["init"]
+    if ini["kind"] == "helix":
+        o.init_helix(ini["axis"], ini["amp"], ini["seed"])
+    else:
+        o.init_uniaxial(ini["n"], ini["amp"], ini["seed"])
+    for c in w["colloids"]:
+        o.add_colloid(c["X"], c["a0"], c["anchoring"], c["w"], c["mobile"], c.get("F_ext"))
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = L**3 * args.steps / dt / 1e6
+    out = dict(metric=METRIC, value=v, unit="MLUPS", n_gpus=ws, steps=args.steps, warmup=args.warmup,
+               ms_per_step=1e3 * dt / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+               dtype="f64", data="synthetic", impl="reference",
+               config=dict(workload=f"{args.workload} (bounded sample: {L}^3 box, same constants and colloid)",
+                           parallelism="host cores"),
+               cpu_baseline=dict(value=v, unit="MLUPS", cores=cores, kind="oracle",
+                                 sample=f"{args.steps} steps of a {L}^3 sample of {args.workload}, {cores} threads"),
+               e2e=dict(value=v, unit="MLUPS", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_gpu(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1102_2193_gb300 as P
+    import synth
+
+    torch.cuda.set_device(local)
+    dist = ws > 1
+    if dist:
+        import torch.distributed as td
+        td.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = synth.workload(args.workload)
+    nx, ny, nz = w["grid"]
+    N = nx * ny * nz
+    stream = torch.cuda.Stream()
+    s = build_box(P, w, stream, P.LC_FP32)
+    nfluid = s.diag()["n_fluid"]
+    s.step(args.warmup)
+    s.synchronize()
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: K graph-replayed steps, inputs resident in HBM ----
+    clk = ClockSampler(local)
+    time.sleep(0.3)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = clk.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * N * args.steps / (ms / 1e3) / 1e6
+
+    # ---- per-phase launch durations: events around each kernel on the launching stream ----
+    prof = s.profile(max(10, min(200, args.steps // 5)))
+    peaks = measured_peaks()
+    lb_ms = prof["lb"]
+    achieved = LB_BYTES * nfluid / (lb_ms / 1e3) / 1e9
+    traffic = ncu_traffic("k_lb", args.workload)
+    step_ms = ms / args.steps
+    step_gbs = STEP_BYTES * N / (step_ms / 1e3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers ----
+    Qh = torch.empty((5, nz, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+    Qo = torch.empty((5, nz, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+    s.get_fields(P.LC_Q, Qh)
+    e2e_steps = args.steps
+    barrier()
+    t0 = time.perf_counter()
+    s.set_fields(P.LC_Q, Qh)
+    s.step(e2e_steps)
+    s.get_fields(P.LC_Q, Qo)
+    forces = s.forces(0)
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([t_e2e], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = dict(value=ws * N * e2e_steps / t_e2e / 1e6, unit="MLUPS",
+               h2d_bytes_per_step=Qh.nbytes / e2e_steps, d2h_bytes_per_step=(Qo.nbytes + 5 * 3 * 8) / e2e_steps,
+               job=f"set_fields(Q, pinned host) + step({e2e_steps}) + get_fields(Q, pinned host) + get_forces")
+    assert np.isfinite(Qo).all() and np.isfinite(forces["F"]).all()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_seconds)
+
+    if rank == 0:
+        out = dict(
+            metric=METRIC, value=value, unit="MLUPS", n_gpus=ws, steps=args.steps, warmup=args.warmup,
+            ms_per_step=step_ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+            data="synthetic",
+            config=dict(workload=args.workload, grid=list(w["grid"]), nodes=N, fluid_nodes=nfluid,
+                        colloid=dict(R=w["colloids"][0]["a0"], anchoring="normal" if w["colloids"][0]["anchoring"] == 0
+                                     else "planar", w=w["colloids"][0]["w"]),
+                        pitch=round(2 * 3.141592653589793 / w["params"]["q0"], 6) if w["params"]["q0"] else None,
+                        storage="FP32 (df deviation, Q) with FP64 reductions",
+                        l2="inputs larger than L2 (state ~0.45 GB per box); no flush", parallelism=f"replicas x{ws}"),
+            roofline=dict(kernel="k_lb (pull collide-stream + bounce-back)", bound="hbm", achieved=achieved,
+                          peak=peaks["hbm"], unit="GB/s", frac=achieved / peaks["hbm"], traffic=traffic,
+                          bytes_per_node=LB_BYTES, units_per_launch=nfluid, launch_ms=lb_ms,
+                          peak_source=f"{peaks['src']} hbm_gbs"),
+            step_roofline=dict(bound="hbm", achieved=step_gbs, peak=peaks["hbm"], unit="GB/s",
+                               frac=step_gbs / peaks["hbm"], bytes_per_node=STEP_BYTES,
+                               note="whole coupled step: 192 B/node algorithmic (df + Q, read + write)"),
+            phase_ms=prof, cpu_baseline=cpu, e2e=e2e, gpu_launches=5 * args.steps, clocks=clocks)
+        print(json.dumps(out), flush=True)
+    if dist:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="chol128_R8")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = setup_dist()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_gpu(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

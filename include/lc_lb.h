@@ -10,8 +10,9 @@
  *     available from lc_lb_last_error(handle) (and lc_lb_last_error(NULL) for
  *     failures that happened before a handle existed);
  *   - device work is queued on the handle's CUDA stream (the one given to
- *     lc_lb_create, NULL = the legacy default stream); calls that return data
- *     to the host synchronise that stream;
+ *     lc_lb_create; NULL = a non-blocking stream the handle creates, since
+ *     the step is captured in a CUDA graph); calls that return data to the
+ *     host synchronise that stream;
  *   - a handle is not thread-safe; distinct handles are independent;
  *   - the handle owns its device memory, taken from the allocator installed
  *     with lc_lb_set_allocator (cudaMalloc/cudaFree when none is installed);
@@ -107,7 +108,8 @@ int lc_lb_set_allocator(lc_alloc_fn alloc, lc_free_fn free_fn, void* ctx);
 
 /* Create a box (Sec. 2: one LB/FD domain).  The state starts as the
  * uniaxial bulk order along z with f at rest equilibrium.  stream is a
- * cudaStream_t (NULL = legacy default stream).  Errors: LC_ERR_ARG for
+ * cudaStream_t other than the legacy default stream (NULL = the handle
+ * creates one).  Errors: LC_ERR_ARG for
  * nx,ny,nz < 1, N >= 2^31, tau <= 1/2, unknown precision; LC_ERR_OOM;
  * LC_ERR_CUDA. */
 int lc_lb_create(const lc_grid* grid, const lc_params* params, void* stream, lc_lb** out);
@@ -171,6 +173,14 @@ int lc_lb_get_colloid(lc_lb* h, int id, double out[27]);
 int lc_lb_get_links(lc_lb* h, int32_t* node, int8_t* dir, int16_t* colloid, size_t cap, size_t* n_out);
 
 int lc_lb_diagnostics(lc_lb* h, lc_diag* out);
+
+/* Profiling: run nsteps steps without the graph, with CUDA events around
+ * each phase on the handle's stream, and return the mean milliseconds per
+ * launch of: [0] LC stress + body force, [1] LB collide/stream, [2] Q
+ * update, [3] link momentum exchange, [4] colloid update.  The state
+ * advances by nsteps.  Synchronises. */
+int lc_lb_profile(lc_lb* h, int nsteps, double ms_out[5]);
+int lc_lb_batch_profile(lc_lb_batch* b, int nsteps, double ms_out[5]);
 int lc_lb_synchronize(lc_lb* h);
 const char* lc_lb_last_error(const lc_lb* h);
 const char* lc_lb_version(void);

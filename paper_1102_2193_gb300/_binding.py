@@ -19,6 +19,7 @@ LC_OK, LC_ERR_ARG, LC_ERR_CUDA, LC_ERR_OOM, LC_ERR_OVERLAP, LC_ERR_NONFINITE, LC
 LC_FP32, LC_FP64 = 0, 1
 LC_NORMAL, LC_PLANAR = 0, 1
 LC_Q, LC_U, LC_RHO, LC_F_PRE, LC_FORCE, LC_SOLID = 0, 1, 2, 3, 4, 5
+PHASES = ("force", "lb", "lc", "links", "colloid")
 _NCOMP = {LC_Q: 5, LC_U: 3, LC_RHO: 1, LC_F_PRE: 19, LC_FORCE: 3, LC_SOLID: 1}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -115,6 +116,8 @@ def lib(use_torch_allocator: bool = True):
         L.lc_lb_get_links.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int8), C.POINTER(C.c_int16),
                                       C.c_size_t, C.POINTER(C.c_size_t)]
         L.lc_lb_diagnostics.argtypes = [vp, C.POINTER(lc_diag)]
+        L.lc_lb_profile.argtypes = [vp, C.c_int, dp]
+        L.lc_lb_batch_profile.argtypes = [vp, C.c_int, dp]
         L.lc_lb_synchronize.argtypes = [vp]
         L.lc_lb_last_error.argtypes = [vp]
         L.lc_lb_last_error.restype = C.c_char_p
@@ -300,6 +303,12 @@ class Solver:
     def synchronize(self):
         self._check(self.L.lc_lb_synchronize(self.h))
 
+    def profile(self, n=10) -> dict:
+        """Mean ms per launch of each phase over n non-graph steps (advances the state)."""
+        ms = np.empty(5)
+        self._check(self.L.lc_lb_profile(self.h, int(n), _dp(ms)))
+        return dict(zip(PHASES, ms.tolist()))
+
     def diag(self) -> dict:
         d = lc_diag()
         self._check(self.L.lc_lb_diagnostics(self.h, C.byref(d)))
@@ -352,6 +361,11 @@ class Batch:
         self._check(self.L.lc_lb_batch_relax(self.h, float(tol), int(max_steps), int(check_every), C.byref(s),
                                              _dp(r)))
         return s.value, r
+
+    def profile(self, n=10) -> dict:
+        ms = np.empty(5)
+        self._check(self.L.lc_lb_batch_profile(self.h, int(n), _dp(ms)))
+        return dict(zip(PHASES, ms.tolist()))
 
     def close(self):
         if getattr(self, "h", None):

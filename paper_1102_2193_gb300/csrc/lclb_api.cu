@@ -1,0 +1,1115 @@
+// lclb_api.cu -- the C ABI of include/lc_lb.h: handles, device memory, the
+// per-step launch sequence (captured once in a CUDA graph and replayed),
+// geometry and boundary-link construction, exports, FP64 diagnostics, the
+// relaxation driver, batches of boxes and the tile autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lc_lb.h"
+#include "lclb_internal.h"
+
+using namespace lclb;
+
+struct Group;
+
+namespace {
+
+struct Allocator {
+  lc_alloc_fn alloc = nullptr;
+  lc_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+Allocator g_alloc;
+std::mutex g_mu;
+thread_local std::string g_err;
+
+struct TileCfg {
+  int ty = 4, zc = 16, persistent = 0;
+};
+
+struct Phase {
+  TileCfg cfg;
+  int4* d_tiles = nullptr;
+  int ntiles = 0;
+  int grid = 0;
+  std::vector<int> start, count;  // per box
+  double* d_part = nullptr;
+  size_t part_cap = 0;
+};
+
+struct Mem {
+  std::vector<std::pair<void*, cudaStream_t>> blocks;
+  void* get(size_t bytes, cudaStream_t s, Allocator& al) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (al.alloc) {
+      p = al.alloc(bytes, (void*)s, al.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      p = nullptr;
+    }
+    if (p) blocks.push_back({p, s});
+    return p;
+  }
+  void put(void* p, Allocator& al) {
+    for (size_t k = 0; k < blocks.size(); ++k)
+      if (blocks[k].first == p) {
+        if (al.free) al.free(p, (void*)blocks[k].second, al.ctx);
+        else cudaFree(p);
+        blocks.erase(blocks.begin() + (long)k);
+        return;
+      }
+  }
+  void release(Allocator& al) {
+    for (auto& b : blocks) {
+      if (al.free) al.free(b.first, (void*)b.second, al.ctx);
+      else cudaFree(b.first);
+    }
+    blocks.clear();
+  }
+};
+
+}  // namespace
+
+struct lc_lb {
+  Group* g = nullptr;
+  int index = 0;
+  bool owns_group = false;
+  lc_grid grid{};
+  lc_params params{};
+  DevBox hb{};                          // host copy of the device descriptor
+  std::vector<DevColloid> col;          // host-side configuration of the colloids
+  int nlinks = 0;
+  std::string err;
+};
+
+struct Group {
+  int prec = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Allocator al;
+  Mem mem;
+  std::vector<lc_lb*> boxes;
+  DevBox* d_boxes = nullptr;
+  Phase ph[3];  // force, lb, lc
+  int2* d_chunks = nullptr;
+  int nchunks = 0, chunk_cap = 0;
+  double* d_scratch = nullptr;  // FP64 export buffer
+  size_t scratch_cap = 0;
+  double* d_red = nullptr;      // reduction outputs
+  double* h_red = nullptr;      // pinned
+  int* d_iwork = nullptr;       // link-build block sums
+  size_t iwork_cap = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool dirty = true, tuned = false;
+  int nsm = 0;
+  std::string err;
+};
+
+struct lc_lb_batch {
+  Group* g = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int fail(std::string* dst, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (dst) *dst = buf;
+  g_err = buf;
+  return code;
+}
+
+#define CK(call, dst)                                                                        \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return fail(dst, LC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t tsize(int prec) { return prec == LC_FP64 ? 8 : 4; }
+
+double bulk_q(double gam) {
+  double t = 1.0 - 8.0 / (3.0 * gam);
+  return t < 0.0 ? 0.0 : 0.25 + 0.75 * std::sqrt(t);
+}
+
+void* galloc(Group* g, size_t bytes) { return g->mem.get(bytes, g->stream, g->al); }
+
+// Tile list of one phase for every box of the group.
+int build_phase(Group* g, int k) {
+  Phase& P = g->ph[k];
+  std::vector<int4> tl;
+  P.start.assign(g->boxes.size(), 0);
+  P.count.assign(g->boxes.size(), 0);
+  for (size_t b = 0; b < g->boxes.size(); ++b) {
+    const lc_grid& G = g->boxes[b]->grid;
+    P.start[b] = (int)tl.size();
+    for (int z = 0; z < G.nz; z += P.cfg.zc)
+      for (int y = 0; y < G.ny; y += P.cfg.ty)
+        for (int x = 0; x < G.nx; x += 32) tl.push_back(make_int4((int)b, x, y, z));
+    P.count[b] = (int)tl.size() - P.start[b];
+  }
+  if (P.d_tiles) g->mem.put(P.d_tiles, g->al);
+  P.ntiles = (int)tl.size();
+  P.d_tiles = (int4*)galloc(g, sizeof(int4) * tl.size());
+  if (!P.d_tiles) return fail(&g->err, LC_ERR_OOM, "tile list allocation failed");
+  CK(cudaMemcpyAsync(P.d_tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice, g->stream), &g->err);
+  const int width = k == 0 ? 1 : (k == 1 ? 4 : 2);
+  const size_t need = (size_t)width * tl.size();
+  if (need > P.part_cap) {
+    if (P.d_part) g->mem.put(P.d_part, g->al);
+    P.d_part = (double*)galloc(g, sizeof(double) * need);
+    if (!P.d_part) return fail(&g->err, LC_ERR_OOM, "partials allocation failed");
+    P.part_cap = need;
+    CK(cudaMemsetAsync(P.d_part, 0, sizeof(double) * need, g->stream), &g->err);
+  }
+  P.grid = P.cfg.persistent ? std::min(P.ntiles, g->nsm * P.cfg.persistent) : P.ntiles;
+  if (P.grid < 1) P.grid = 1;
+  g->dirty = true;
+  return LC_OK;
+}
+
+Launch phase_launch(Group* g, int k, int box = -1) {
+  Phase& P = g->ph[k];
+  Launch L;
+  L.boxes = g->d_boxes;
+  L.zc = P.cfg.zc;
+  L.ty = P.cfg.ty;
+  L.stream = g->stream;
+  if (box < 0) {
+    L.tiles = P.d_tiles;
+    L.ntiles = P.ntiles;
+    L.grid = P.grid;
+  } else {
+    L.tiles = P.d_tiles + P.start[box];
+    L.ntiles = P.count[box];
+    L.grid = P.count[box];
+  }
+  return L;
+}
+
+int upload_box(Group* g, lc_lb* h) {
+  CK(cudaMemcpyAsync(g->d_boxes + h->index, &h->hb, sizeof(DevBox), cudaMemcpyHostToDevice, g->stream), &h->err);
+  g->dirty = true;
+  return LC_OK;
+}
+
+// Link chunks (box, first link) covering every box's link capacity.
+int build_chunks(Group* g) {
+  std::vector<int2> ch;
+  for (size_t b = 0; b < g->boxes.size(); ++b) {
+    const lc_lb* h = g->boxes[b];
+    for (int s = 0; s < h->hb.nlinks_cap; s += 256) ch.push_back(make_int2((int)b, s));
+  }
+  if ((int)ch.size() > g->chunk_cap) {
+    if (g->d_chunks) g->mem.put(g->d_chunks, g->al);
+    g->chunk_cap = (int)ch.size() + 64;
+    g->d_chunks = (int2*)galloc(g, sizeof(int2) * g->chunk_cap);
+    if (!g->d_chunks) return fail(&g->err, LC_ERR_OOM, "link chunk allocation failed");
+  }
+  g->nchunks = (int)ch.size();
+  if (!ch.empty())
+    CK(cudaMemcpyAsync(g->d_chunks, ch.data(), sizeof(int2) * ch.size(), cudaMemcpyHostToDevice, g->stream), &g->err);
+  g->dirty = true;
+  return LC_OK;
+}
+
+int ensure_scratch(Group* g, size_t doubles) {
+  if (doubles <= g->scratch_cap) return LC_OK;
+  if (g->d_scratch) g->mem.put(g->d_scratch, g->al);
+  g->d_scratch = (double*)galloc(g, sizeof(double) * doubles);
+  if (!g->d_scratch) return fail(&g->err, LC_ERR_OOM, "scratch allocation failed");
+  g->scratch_cap = doubles;
+  return LC_OK;
+}
+
+int ensure_iwork(Group* g, size_t ints) {
+  if (ints <= g->iwork_cap) return LC_OK;
+  if (g->d_iwork) g->mem.put(g->d_iwork, g->al);
+  g->d_iwork = (int*)galloc(g, sizeof(int) * ints);
+  if (!g->d_iwork) return fail(&g->err, LC_ERR_OOM, "work allocation failed");
+  g->iwork_cap = ints;
+  return LC_OK;
+}
+
+int check_params(const lc_grid* G, const lc_params* p, std::string* err) {
+  if (!G || !p) return fail(err, LC_ERR_ARG, "null grid or params");
+  if (G->nx < 1 || G->ny < 1 || G->nz < 1) return fail(err, LC_ERR_ARG, "box dimensions must be >= 1");
+  if ((long long)G->nx * G->ny * G->nz >= (1LL << 31) - 1) return fail(err, LC_ERR_ARG, "box too large (N >= 2^31)");
+  if (!(p->tau > 0.5)) return fail(err, LC_ERR_ARG, "tau must exceed 1/2");
+  if (p->precision != LC_FP32 && p->precision != LC_FP64) return fail(err, LC_ERR_ARG, "unknown precision");
+  if (!(p->rho0 > 0.0)) return fail(err, LC_ERR_ARG, "rho0 must be positive");
+  return LC_OK;
+}
+
+int write_state(Group* g, lc_lb* h, int pre_valid) {
+  DevState st{};
+  st.fpar = 0;
+  st.qpar = 0;
+  st.pre_valid = pre_valid;
+  CK(cudaMemcpyAsync(h->hb.st, &st, sizeof(st), cudaMemcpyHostToDevice, g->stream), &h->err);
+  return LC_OK;
+}
+
+template <typename T>
+void fill_phys(PhysT<T>& o, const DevParams& p) {
+  o.rho0 = (T)p.rho0;
+  o.omega = (T)(1.0 / p.tau);
+  o.pref = (T)(1.0 - 0.5 / p.tau);
+  o.A0 = (T)p.A0; o.gamma = (T)p.gamma; o.K = (T)p.K; o.q0 = (T)p.q0; o.xi = (T)p.xi; o.Gamma = (T)p.Gamma;
+  o.S0 = (T)p.S0;
+  for (int a = 0; a < 3; ++a) o.g[a] = (T)p.g[a];
+}
+
+// Allocate and initialise one box inside group g.
+int make_box(Group* g, const lc_grid* G, const lc_params* p, lc_lb* h) {
+  h->grid = *G;
+  h->params = *p;
+  DevBox& B = h->hb;
+  memset(&B, 0, sizeof(B));
+  B.nx = G->nx; B.ny = G->ny; B.nz = G->nz; B.wall_z = G->wall_z ? 1 : 0;
+  B.N = G->nx * G->ny * G->nz;
+  const size_t N = (size_t)B.N, ts = tsize(g->prec);
+  B.p.rho0 = p->rho0; B.p.tau = p->tau; B.p.A0 = p->A0; B.p.gamma = p->gamma; B.p.K = p->K; B.p.q0 = p->q0;
+  B.p.xi = p->xi; B.p.Gamma = p->Gamma; B.p.S0 = p->S0 > 0.0 ? p->S0 : bulk_q(p->gamma);
+  for (int a = 0; a < 3; ++a) B.p.g[a] = p->body_force[a];
+  B.p.lc_on = p->lc_enabled ? 1 : 0;
+  B.p.flow_on = p->flow_enabled ? 1 : 0;
+  fill_phys(B.pf, B.p);
+  fill_phys(B.pd, B.p);
+  for (int k = 0; k < 2; ++k) {
+    B.f[k] = galloc(g, NQ * N * ts);
+    B.Q[k] = galloc(g, 5 * N * ts);
+  }
+  B.u = galloc(g, 3 * N * ts);
+  B.F = galloc(g, 3 * N * ts);
+  B.mask = (uint8_t*)galloc(g, N);
+  B.col = (DevColloid*)galloc(g, sizeof(DevColloid) * MAXCOL);
+  B.st = (DevState*)galloc(g, sizeof(DevState));
+  B.nlinks = (int*)galloc(g, sizeof(int));
+  if (!B.f[0] || !B.f[1] || !B.Q[0] || !B.Q[1] || !B.u || !B.F || !B.mask || !B.col || !B.st || !B.nlinks)
+    return fail(&h->err, LC_ERR_OOM, "device allocation failed for a %dx%dx%d box", G->nx, G->ny, G->nz);
+  cudaStream_t s = g->stream;
+  for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(B.f[k], 0, NQ * N * ts, s), &h->err);
+  CK(cudaMemsetAsync(B.u, 0, 3 * N * ts, s), &h->err);
+  CK(cudaMemsetAsync(B.F, 0, 3 * N * ts, s), &h->err);
+  CK(cudaMemsetAsync(B.mask, 0, N, s), &h->err);
+  CK(cudaMemsetAsync(B.col, 0, sizeof(DevColloid) * MAXCOL, s), &h->err);
+  CK(cudaMemsetAsync(B.nlinks, 0, sizeof(int), s), &h->err);
+  int rc = write_state(g, h, 1);
+  if (rc) return rc;
+  rc = upload_box(g, h);
+  if (rc) return rc;
+  const double n[3] = {0.0, 0.0, 1.0};
+  CK(launch_geometry(g->d_boxes, h->index, B.N, s), &h->err);
+  CK(launch_init_q(g->prec, g->d_boxes, h->index, B.N, 0, n, 0.0, 0ULL, s), &h->err);
+  return LC_OK;
+}
+
+Group* new_group(int prec, void* stream, int nboxes, std::string* err) {
+  Group* g = new Group();
+  g->prec = prec;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g->al = g_alloc;
+  }
+  if (stream) {
+    g->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      fail(err, LC_ERR_CUDA, "cannot create a stream");
+      delete g;
+      return nullptr;
+    }
+    g->own_stream = true;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (g->nsm <= 0) g->nsm = 1;
+  g->d_boxes = (DevBox*)galloc(g, sizeof(DevBox) * std::max(1, nboxes));
+  g->d_red = (double*)galloc(g, sizeof(double) * 64);
+  if (!g->d_boxes || !g->d_red || cudaMallocHost(&g->h_red, sizeof(double) * 64) != cudaSuccess) {
+    fail(err, LC_ERR_OOM, "group allocation failed");
+    g->mem.release(g->al);
+    if (g->own_stream) cudaStreamDestroy(g->stream);
+    delete g;
+    return nullptr;
+  }
+  return g;
+}
+
+void free_group(Group* g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->stream);
+  if (g->gexec) cudaGraphExecDestroy(g->gexec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  g->mem.release(g->al);
+  if (g->h_red) cudaFreeHost(g->h_red);
+  if (g->own_stream) cudaStreamDestroy(g->stream);
+  for (lc_lb* h : g->boxes) delete h;
+  delete g;
+}
+
+// ---- autotuning -------------------------------------------------------------
+using TuneKey = std::tuple<long long, int>;  // (sum of box signature, precision)
+std::map<TuneKey, std::vector<TileCfg>> g_tune_cache;
+
+TuneKey tune_key(Group* g) {
+  long long sig = 1469598103934665603LL;
+  for (lc_lb* h : g->boxes) {
+    sig = sig * 1099511628211LL + h->grid.nx;
+    sig = sig * 1099511628211LL + h->grid.ny;
+    sig = sig * 1099511628211LL + h->grid.nz;
+    sig = sig * 1099511628211LL + h->grid.wall_z;
+  }
+  return TuneKey(sig, g->prec);
+}
+
+// Optional file cache (LCLB_TUNE_CACHE): one line per entry,
+// "signature precision ty zc persistent x3".
+void tune_file_load() {
+  const char* path = getenv("LCLB_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  long long sig;
+  int prec, v[9];
+  while (fscanf(f, "%lld %d %d %d %d %d %d %d %d %d %d", &sig, &prec, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
+                &v[7], &v[8]) == 11) {
+    std::vector<TileCfg> c(3);
+    for (int k = 0; k < 3; ++k) c[k] = TileCfg{v[3 * k], v[3 * k + 1], v[3 * k + 2]};
+    g_tune_cache[TuneKey(sig, prec)] = c;
+  }
+  fclose(f);
+}
+
+void tune_file_store(const TuneKey& key, const std::vector<TileCfg>& c) {
+  const char* path = getenv("LCLB_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%lld %d", std::get<0>(key), std::get<1>(key));
+  for (int k = 0; k < 3; ++k) fprintf(f, " %d %d %d", c[k].ty, c[k].zc, c[k].persistent);
+  fprintf(f, "\n");
+  fclose(f);
+}
+
+cudaError_t launch_phase(Group* g, int k, int mode, int box = -1) {
+  Launch L = phase_launch(g, k, box);
+  double* part = g->ph[k].d_part + (box < 0 ? 0 : (size_t)g->ph[k].start[box] * (k == 0 ? 1 : (k == 1 ? 4 : 2)));
+  if (k == 0) return launch_force(g->prec, L, mode, part);
+  if (k == 1) return launch_lb(g->prec, L, mode, part);
+  return launch_lc(g->prec, L, mode, part);
+}
+
+// Time every candidate tile shape of each phase on the group's own state (the
+// phase kernels are idempotent between parity flips) and keep the fastest.
+int autotune_group(Group* g, std::string* desc) {
+  const int tys[3] = {2, 4, 8};
+  const int zcs[7] = {1, 2, 4, 8, 16, 32, 64};
+  const int pers[3] = {0, 4, 8};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), &g->err);
+  CK(cudaEventCreate(&e1), &g->err);
+  char buf[256];
+  std::string out;
+  for (int k = 0; k < 3; ++k) {
+    TileCfg best = g->ph[k].cfg;
+    float best_ms = 1e30f;
+    for (int ty : tys)
+      for (int zc : zcs)
+        for (int pp : pers) {
+          if (k == 0 && g->prec == LC_FP64 && ty == 8) continue;
+          g->ph[k].cfg = TileCfg{ty, zc, pp};
+          if (build_phase(g, k)) return LC_ERR_OOM;
+          const int mode = k == 2 ? LC_RESID : 0;
+          CK(launch_phase(g, k, mode), &g->err);  // warm-up
+          CK(cudaEventRecord(e0, g->stream), &g->err);
+          for (int r = 0; r < 3; ++r) CK(launch_phase(g, k, mode), &g->err);
+          CK(cudaEventRecord(e1, g->stream), &g->err);
+          CK(cudaEventSynchronize(e1), &g->err);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = g->ph[k].cfg;
+          }
+        }
+    g->ph[k].cfg = best;
+    if (build_phase(g, k)) return LC_ERR_OOM;
+    snprintf(buf, sizeof(buf), "%s:ty=%d,zc=%d,pers=%d(%.1fus) ", k == 0 ? "force" : (k == 1 ? "lb" : "lc"), best.ty,
+             best.zc, best.persistent, 1000.f * best_ms / 3.f);
+    out += buf;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tune_cache[tune_key(g)] = {g->ph[0].cfg, g->ph[1].cfg, g->ph[2].cfg};
+    tune_file_store(tune_key(g), g_tune_cache[tune_key(g)]);
+  }
+  g->tuned = true;
+  if (desc) *desc = out;
+  return LC_OK;
+}
+
+int maybe_tune(Group* g) {
+  if (g->tuned) return LC_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    static bool loaded = false;
+    if (!loaded) {
+      tune_file_load();
+      loaded = true;
+    }
+    auto it = g_tune_cache.find(tune_key(g));
+    if (it != g_tune_cache.end()) {
+      for (int k = 0; k < 3; ++k) g->ph[k].cfg = it->second[k];
+      g->tuned = true;
+    }
+  }
+  if (g->tuned) {
+    for (int k = 0; k < 3; ++k)
+      if (build_phase(g, k)) return LC_ERR_OOM;
+    return LC_OK;
+  }
+  const char* env = getenv("LCLB_AUTOTUNE");
+  if (env && env[0] == '0') {
+    g->tuned = true;
+    return LC_OK;
+  }
+  return autotune_group(g, nullptr);
+}
+
+// ---- one step -----------------------------------------------------------------
+int enqueue_step(Group* g) {
+  CK(launch_phase(g, 0, FORCE_ACC), &g->err);
+  CK(launch_phase(g, 1, 0), &g->err);
+  CK(launch_phase(g, 2, LC_RESID), &g->err);
+  CK(launch_links(g->prec, g->d_boxes, g->d_chunks, g->nchunks, g->nchunks, g->stream), &g->err);
+  CK(launch_colloid(g->d_boxes, (int)g->boxes.size(), g->stream), &g->err);
+  return LC_OK;
+}
+
+int capture(Group* g) {
+  if (!g->dirty && g->gexec) return LC_OK;
+  if (g->gexec) {
+    cudaGraphExecDestroy(g->gexec);
+    g->gexec = nullptr;
+  }
+  if (g->graph) {
+    cudaGraphDestroy(g->graph);
+    g->graph = nullptr;
+  }
+  CK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal), &g->err);
+  int rc = enqueue_step(g);
+  cudaGraph_t gr = nullptr;
+  cudaError_t e = cudaStreamEndCapture(g->stream, &gr);
+  if (rc) {
+    if (gr) cudaGraphDestroy(gr);
+    return rc;
+  }
+  CK(e, &g->err);
+  g->graph = gr;
+  CK(cudaGraphInstantiate(&g->gexec, gr, 0), &g->err);
+  g->dirty = false;
+  return LC_OK;
+}
+
+// Non-graph steps with events around each phase; mean ms per launch.
+int group_profile(Group* g, int n, double* ms) {
+  int rc = maybe_tune(g);
+  if (rc) return rc;
+  cudaEvent_t ev[6];
+  for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&ev[k]), &g->err);
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int s = 0; s < n; ++s) {
+    CK(cudaEventRecord(ev[0], g->stream), &g->err);
+    CK(launch_phase(g, 0, FORCE_ACC), &g->err);
+    CK(cudaEventRecord(ev[1], g->stream), &g->err);
+    CK(launch_phase(g, 1, 0), &g->err);
+    CK(cudaEventRecord(ev[2], g->stream), &g->err);
+    CK(launch_phase(g, 2, LC_RESID), &g->err);
+    CK(cudaEventRecord(ev[3], g->stream), &g->err);
+    CK(launch_links(g->prec, g->d_boxes, g->d_chunks, g->nchunks, g->nchunks, g->stream), &g->err);
+    CK(cudaEventRecord(ev[4], g->stream), &g->err);
+    CK(launch_colloid(g->d_boxes, (int)g->boxes.size(), g->stream), &g->err);
+    CK(cudaEventRecord(ev[5], g->stream), &g->err);
+    CK(cudaEventSynchronize(ev[5]), &g->err);
+    for (int k = 0; k < 5; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      acc[k] += t;
+    }
+  }
+  for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < 5; ++k) ms[k] = n > 0 ? acc[k] / n : 0.0;
+  return LC_OK;
+}
+
+int group_step(Group* g, int n) {
+  if (n < 0) return fail(&g->err, LC_ERR_ARG, "negative step count");
+  if (n == 0) return LC_OK;
+  int rc = maybe_tune(g);
+  if (rc) return rc;
+  const char* env = getenv("LCLB_NO_GRAPH");
+  if (env && env[0] == '1') {
+    for (int s = 0; s < n; ++s)
+      if ((rc = enqueue_step(g))) return rc;
+    return LC_OK;
+  }
+  if ((rc = capture(g))) return rc;
+  for (int s = 0; s < n; ++s) CK(cudaGraphLaunch(g->gexec, g->stream), &g->err);
+  return LC_OK;
+}
+
+// Residual (RMS, max) of the last step of box b -> h_red[0..1] (synchronises).
+int box_residual(Group* g, int b, double* rms, double* mx, long long nfluid) {
+  Phase& P = g->ph[2];
+  CK(launch_reduce(P.d_part, P.start[b], P.count[b], 2, 2u, g->d_red, g->stream), &g->err);
+  CK(cudaMemcpyAsync(g->h_red, g->d_red, 2 * sizeof(double), cudaMemcpyDeviceToHost, g->stream), &g->err);
+  CK(cudaStreamSynchronize(g->stream), &g->err);
+  *rms = nfluid > 0 ? std::sqrt(g->h_red[0] / (double)nfluid) : 0.0;
+  *mx = g->h_red[1];
+  return LC_OK;
+}
+
+int count_fluid(Group* g, lc_lb* h, long long* nf, long long* ndef, double* sums) {
+  const int nb = diag_state_blocks(h->hb.N);
+  int rc = ensure_scratch(g, (size_t)6 * nb);
+  if (rc) return rc;
+  CK(launch_diag_state(g->prec, g->d_boxes, h->index, h->hb.N, g->d_scratch, g->stream), &h->err);
+  CK(launch_reduce(g->d_scratch, 0, nb, 6, 0u, g->d_red, g->stream), &h->err);
+  CK(cudaMemcpyAsync(g->h_red, g->d_red, 6 * sizeof(double), cudaMemcpyDeviceToHost, g->stream), &h->err);
+  CK(cudaStreamSynchronize(g->stream), &h->err);
+  if (sums)
+    for (int k = 0; k < 4; ++k) sums[k] = g->h_red[k];
+  *nf = (long long)llround(g->h_red[4]);
+  if (ndef) *ndef = (long long)llround(g->h_red[5]);
+  return LC_OK;
+}
+
+int rebuild_geometry(lc_lb* h) {
+  Group* g = h->g;
+  cudaStream_t s = g->stream;
+  int rc = upload_box(g, h);
+  if (rc) return rc;
+  CK(launch_geometry(g->d_boxes, h->index, h->hb.N, s), &h->err);
+  // boundary links, colloid by colloid, in node order
+  const int nb = (h->hb.N + 255) / 256;
+  if ((rc = ensure_iwork(g, (size_t)nb + 8))) return rc;
+  int total = 0;
+  std::vector<int> counts(h->col.size());
+  for (size_t c = 0; c < h->col.size(); ++c) {
+    CK(launch_link_build(g->d_boxes, h->index, h->hb.N, (int)c, g->d_iwork, total, g->d_iwork + nb, s), &h->err);
+    int t = 0;
+    CK(cudaMemcpyAsync(&t, g->d_iwork + nb, sizeof(int), cudaMemcpyDeviceToHost, s), &h->err);
+    CK(cudaStreamSynchronize(s), &h->err);
+    total = t;
+  }
+  if (total > h->hb.nlinks_cap) {
+    if (h->hb.link_node) {
+      g->mem.put(h->hb.link_node, g->al);
+      g->mem.put(h->hb.link_dir, g->al);
+      g->mem.put(h->hb.link_col, g->al);
+    }
+    const int cap = total + total / 2 + 256;
+    h->hb.link_node = (int*)galloc(g, sizeof(int) * cap);
+    h->hb.link_dir = (int8_t*)galloc(g, cap);
+    h->hb.link_col = (int8_t*)galloc(g, cap);
+    if (!h->hb.link_node || !h->hb.link_dir || !h->hb.link_col) return fail(&h->err, LC_ERR_OOM, "link allocation");
+    h->hb.nlinks_cap = cap;
+    if ((rc = upload_box(g, h))) return rc;
+    total = 0;
+    for (size_t c = 0; c < h->col.size(); ++c) {
+      CK(launch_link_build(g->d_boxes, h->index, h->hb.N, (int)c, g->d_iwork, total, g->d_iwork + nb, s), &h->err);
+      int t = 0;
+      CK(cudaMemcpyAsync(&t, g->d_iwork + nb, sizeof(int), cudaMemcpyDeviceToHost, s), &h->err);
+      CK(cudaStreamSynchronize(s), &h->err);
+      total = t;
+    }
+  }
+  CK(cudaMemcpyAsync(h->hb.nlinks, &total, sizeof(int), cudaMemcpyHostToDevice, s), &h->err);
+  h->nlinks = total;
+  if ((rc = build_chunks(g))) return rc;
+  CK(cudaStreamSynchronize(s), &h->err);
+  return LC_OK;
+}
+
+int h_check(lc_lb* h) {
+  if (!h) return fail(nullptr, LC_ERR_ARG, "null handle");
+  return LC_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+int lc_lb_set_allocator(lc_alloc_fn alloc, lc_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return fail(nullptr, LC_ERR_ARG, "alloc and free must both be set");
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.free = free_fn;
+  g_alloc.ctx = ctx;
+  return LC_OK;
+}
+
+const char* lc_lb_version(void) { return "lclb 0.1 (sm_103a)"; }
+
+int lc_lb_create(const lc_grid* grid, const lc_params* params, void* stream, lc_lb** out) {
+  if (!out) return fail(nullptr, LC_ERR_ARG, "null output pointer");
+  *out = nullptr;
+  std::string err;
+  int rc = check_params(grid, params, &err);
+  if (rc) return rc;
+  Group* g = new_group(params->precision, stream, 1, &err);
+  if (!g) return LC_ERR_OOM;
+  lc_lb* h = new lc_lb();
+  h->g = g;
+  h->index = 0;
+  h->owns_group = true;
+  g->boxes.push_back(h);
+  rc = make_box(g, grid, params, h);
+  if (!rc) rc = rebuild_geometry(h);
+  for (int k = 0; k < 3 && !rc; ++k) rc = build_phase(g, k);
+  if (!rc) rc = build_chunks(g);
+  if (rc) {
+    g_err = h->err.empty() ? g->err : h->err;
+    free_group(g);
+    return rc;
+  }
+  CK(cudaStreamSynchronize(g->stream), nullptr);
+  *out = h;
+  return LC_OK;
+}
+
+void lc_lb_destroy(lc_lb* h) {
+  if (!h || !h->owns_group) return;
+  free_group(h->g);
+}
+
+int lc_lb_init_uniaxial(lc_lb* h, const double n[3], double noise_amp, uint64_t seed) {
+  if (int rc = h_check(h)) return rc;
+  if (!n || !(n[0] * n[0] + n[1] * n[1] + n[2] * n[2] > 0.0)) return fail(&h->err, LC_ERR_ARG, "director must be non-zero");
+  Group* g = h->g;
+  const size_t N = (size_t)h->hb.N, ts = tsize(g->prec);
+  CK(launch_init_q(g->prec, g->d_boxes, h->index, h->hb.N, 0, n, noise_amp, (unsigned long long)seed, g->stream),
+     &h->err);
+  for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(h->hb.f[k], 0, NQ * N * ts, g->stream), &h->err);
+  CK(cudaMemsetAsync(h->hb.u, 0, 3 * N * ts, g->stream), &h->err);
+  return write_state(g, h, 1);
+}
+
+int lc_lb_init_helix(lc_lb* h, int axis, double noise_amp, uint64_t seed) {
+  if (int rc = h_check(h)) return rc;
+  if (axis < 0 || axis > 2) return fail(&h->err, LC_ERR_ARG, "axis must be 0, 1 or 2");
+  Group* g = h->g;
+  const size_t N = (size_t)h->hb.N, ts = tsize(g->prec);
+  const double n[3] = {(double)axis, 0.0, 0.0};
+  CK(launch_init_q(g->prec, g->d_boxes, h->index, h->hb.N, 1, n, noise_amp, (unsigned long long)seed, g->stream),
+     &h->err);
+  for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(h->hb.f[k], 0, NQ * N * ts, g->stream), &h->err);
+  CK(cudaMemsetAsync(h->hb.u, 0, 3 * N * ts, g->stream), &h->err);
+  return write_state(g, h, 1);
+}
+
+int lc_lb_set_fields(lc_lb* h, int which, const void* src, size_t bytes, int src_is_device) {
+  if (int rc = h_check(h)) return rc;
+  Group* g = h->g;
+  const size_t N = (size_t)h->hb.N;
+  size_t nc = which == LC_Q ? 5 : (which == LC_F_PRE ? NQ : 0);
+  if (!nc) return fail(&h->err, LC_ERR_ARG, "only LC_Q and LC_F_PRE can be set");
+  if (!src || bytes != nc * N * sizeof(double)) return fail(&h->err, LC_ERR_ARG, "expected %zu bytes", nc * N * 8);
+  int rc = ensure_scratch(g, nc * N);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(g->d_scratch, src, bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     g->stream),
+     &h->err);
+  if (which == LC_F_PRE) {
+    // the pre-collision state goes into the current buffer and is read in place
+    DevState st{};
+    CK(cudaMemcpyAsync(&st, h->hb.st, sizeof(st), cudaMemcpyDeviceToHost, g->stream), &h->err);
+    CK(cudaStreamSynchronize(g->stream), &h->err);
+    CK(launch_set_field(g->prec, g->d_boxes, h->index, h->hb.N, 1, g->d_scratch, g->stream), &h->err);
+    st.pre_valid = 1;
+    CK(cudaMemcpyAsync(h->hb.st, &st, sizeof(st), cudaMemcpyHostToDevice, g->stream), &h->err);
+  } else {
+    CK(launch_set_field(g->prec, g->d_boxes, h->index, h->hb.N, 0, g->d_scratch, g->stream), &h->err);
+  }
+  CK(cudaStreamSynchronize(g->stream), &h->err);
+  return LC_OK;
+}
+
+int lc_lb_add_colloid(lc_lb* h, const double X[3], double a0, int anchoring, double w, int mobile,
+                      const double F_ext[3], int* id_out) {
+  if (int rc = h_check(h)) return rc;
+  if (!X || !(a0 > 0.0)) return fail(&h->err, LC_ERR_ARG, "bad colloid position or radius");
+  if ((int)h->col.size() >= MAXCOL) return fail(&h->err, LC_ERR_ARG, "too many colloids (max %d)", MAXCOL);
+  if (anchoring != LC_NORMAL && anchoring != LC_PLANAR) return fail(&h->err, LC_ERR_ARG, "unknown anchoring");
+  if (h->grid.wall_z && (X[2] - a0 < -0.5 || X[2] + a0 > h->grid.nz - 0.5))
+    return fail(&h->err, LC_ERR_OVERLAP, "colloid crosses a wall");
+  Group* g = h->g;
+  DevColloid C;
+  memset(&C, 0, sizeof(C));
+  for (int a = 0; a < 3; ++a) {
+    C.X[a] = C.Xb[a] = X[a];
+    C.Fext[a] = F_ext ? F_ext[a] : 0.0;
+  }
+  C.a0 = a0;
+  C.w = w;
+  C.strong = (!(w > 0.0) || std::isinf(w)) ? 1 : 0;
+  C.anchoring = anchoring;
+  C.mobile = mobile ? 1 : 0;
+  C.M = h->params.rho0 * 4.0 / 3.0 * M_PI * a0 * a0 * a0;
+  C.I = 0.4 * C.M * a0 * a0;
+  const int id = (int)h->col.size();
+  CK(cudaMemcpyAsync(h->hb.col + id, &C, sizeof(C), cudaMemcpyHostToDevice, g->stream), &h->err);
+  h->col.push_back(C);
+  h->hb.ncol = (int)h->col.size();
+  int rc = rebuild_geometry(h);
+  if (rc) return rc;
+  DevState st{};
+  CK(cudaMemcpyAsync(&st, h->hb.st, sizeof(st), cudaMemcpyDeviceToHost, g->stream), &h->err);
+  CK(cudaStreamSynchronize(g->stream), &h->err);
+  if (st.err & 4) {
+    h->col.pop_back();
+    h->hb.ncol = (int)h->col.size();
+    st.err &= ~4;
+    CK(cudaMemcpyAsync(h->hb.st, &st, sizeof(st), cudaMemcpyHostToDevice, g->stream), &h->err);
+    rc = rebuild_geometry(h);
+    if (rc) return rc;
+    return fail(&h->err, LC_ERR_OVERLAP, "colloid overlaps another colloid");
+  }
+  if (id_out) *id_out = id;
+  return LC_OK;
+}
+
+static int colloid_rmw(lc_lb* h, int id, const double* V, const double* W, const double* Fext) {
+  if (int rc = h_check(h)) return rc;
+  if (id < 0 || id >= (int)h->col.size()) return fail(&h->err, LC_ERR_ARG, "no colloid %d", id);
+  Group* g = h->g;
+  DevColloid C;
+  CK(cudaMemcpyAsync(&C, h->hb.col + id, sizeof(C), cudaMemcpyDeviceToHost, g->stream), &h->err);
+  CK(cudaStreamSynchronize(g->stream), &h->err);
+  for (int a = 0; a < 3; ++a) {
+    if (V) C.V[a] = C.Vb[a] = V[a];
+    if (W) C.W[a] = C.Wb[a] = W[a];
+    if (Fext) C.Fext[a] = Fext[a];
+  }
+  CK(cudaMemcpyAsync(h->hb.col + id, &C, sizeof(C), cudaMemcpyHostToDevice, g->stream), &h->err);
+  CK(cudaStreamSynchronize(g->stream), &h->err);
+  return LC_OK;
+}
+
+int lc_lb_set_colloid_velocity(lc_lb* h, int id, const double V[3], const double W[3]) {
+  return colloid_rmw(h, id, V, W, nullptr);
+}
+
+int lc_lb_set_colloid_force(lc_lb* h, int id, const double F_ext[3]) { return colloid_rmw(h, id, nullptr, nullptr, F_ext); }
+
+int lc_lb_step(lc_lb* h, int nsteps) {
+  if (int rc = h_check(h)) return rc;
+  if (!h->owns_group) return fail(&h->err, LC_ERR_STATE, "box of a batch: step the batch");
+  int rc = group_step(h->g, nsteps);
+  if (rc) h->err = h->g->err;
+  return rc;
+}
+
+int lc_lb_synchronize(lc_lb* h) {
+  if (int rc = h_check(h)) return rc;
+  CK(cudaStreamSynchronize(h->g->stream), &h->err);
+  return LC_OK;
+}
+
+int lc_lb_relax(lc_lb* h, double tol, long long max_steps, int check_every, long long* steps_out, double* resid_out) {
+  if (int rc = h_check(h)) return rc;
+  if (!h->owns_group) return fail(&h->err, LC_ERR_STATE, "box of a batch: relax the batch");
+  if (check_every < 1 || max_steps < 0) return fail(&h->err, LC_ERR_ARG, "bad relax arguments");
+  Group* g = h->g;
+  long long nf = 0;
+  int rc = count_fluid(g, h, &nf, nullptr, nullptr);
+  if (rc) return rc;
+  long long done = 0;
+  double rms = INFINITY, mx = 0.0;
+  while (done < max_steps) {
+    const int n = (int)std::min<long long>(check_every, max_steps - done);
+    if ((rc = group_step(g, n))) {
+      h->err = g->err;
+      return rc;
+    }
+    done += n;
+    if ((rc = box_residual(g, h->index, &rms, &mx, nf))) return rc;
+    if (!std::isfinite(rms)) {
+      if (steps_out) *steps_out = done;
+      if (resid_out) *resid_out = rms;
+      return fail(&h->err, LC_ERR_NONFINITE, "residual is not finite after %lld steps", done);
+    }
+    if (rms <= tol) break;
+  }
+  if (steps_out) *steps_out = done;
+  if (resid_out) *resid_out = rms;
+  return LC_OK;
+}
+
+int lc_lb_get_fields(lc_lb* h, int which, void* dst, size_t bytes, int dst_is_device) {
+  if (int rc = h_check(h)) return rc;
+  Group* g = h->g;
+  const size_t N = (size_t)h->hb.N;
+  size_t nc = 0;
+  switch (which) {
+    case LC_Q: nc = 5; break;
+    case LC_U: nc = 3; break;
+    case LC_RHO: nc = 1; break;
+    case LC_F_PRE: nc = NQ; break;
+    case LC_FORCE: nc = 3; break;
+    case LC_SOLID: nc = 1; break;
+    default: return fail(&h->err, LC_ERR_ARG, "unknown field %d", which);
+  }
+  if (!dst || bytes < nc * N * sizeof(double)) return fail(&h->err, LC_ERR_ARG, "destination too small");
+  int rc = ensure_scratch(g, nc * N);
+  if (rc) return rc;
+  if ((which == LC_U || which == LC_FORCE) && h->hb.p.lc_on) {
+    // body force of the current Q (no colloid accumulation)
+    CK(launch_phase(g, 0, 0, h->index), &h->err);
+  }
+  CK(launch_export(g->prec, g->d_boxes, h->index, h->hb.N, which, g->d_scratch, g->stream), &h->err);
+  CK(cudaMemcpyAsync(dst, g->d_scratch, nc * N * sizeof(double),
+                     dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream),
+     &h->err);
+  CK(cudaStreamSynchronize(g->stream), &h->err);
+  return LC_OK;
+}
+
+int lc_lb_get_colloid(lc_lb* h, int id, double out[27]) {
+  if (int rc = h_check(h)) return rc;
+  if (id < 0 || id >= (int)h->col.size() || !out) return fail(&h->err, LC_ERR_ARG, "no colloid %d", id);
+  DevColloid C;
+  CK(cudaMemcpyAsync(&C, h->hb.col + id, sizeof(C), cudaMemcpyDeviceToHost, h->g->stream), &h->err);
+  CK(cudaStreamSynchronize(h->g->stream), &h->err);
+  const double* src[9] = {C.X, C.V, C.W, C.Fh, C.Th, C.Flc, C.Tlc, C.imp, C.aimp};
+  for (int k = 0; k < 9; ++k)
+    for (int a = 0; a < 3; ++a) out[3 * k + a] = src[k][a];
+  return LC_OK;
+}
+
+int lc_lb_get_forces(lc_lb* h, int id, double F[3], double T[3], double V[3], double W[3], double X[3]) {
+  double r[27];
+  int rc = lc_lb_get_colloid(h, id, r);
+  if (rc) return rc;
+  for (int a = 0; a < 3; ++a) {
+    if (F) F[a] = r[9 + a] + r[15 + a];
+    if (T) T[a] = r[12 + a] + r[18 + a];
+    if (V) V[a] = r[3 + a];
+    if (W) W[a] = r[6 + a];
+    if (X) X[a] = r[a];
+  }
+  return LC_OK;
+}
+
+int lc_lb_get_links(lc_lb* h, int32_t* node, int8_t* dir, int16_t* colloid, size_t cap, size_t* n_out) {
+  if (int rc = h_check(h)) return rc;
+  Group* g = h->g;
+  int n = 0;
+  CK(cudaMemcpyAsync(&n, h->hb.nlinks, sizeof(int), cudaMemcpyDeviceToHost, g->stream), &h->err);
+  CK(cudaStreamSynchronize(g->stream), &h->err);
+  if (n_out) *n_out = (size_t)n;
+  const size_t k = std::min(cap, (size_t)n);
+  if (k == 0) return LC_OK;
+  std::vector<int8_t> c8(k);
+  if (node) CK(cudaMemcpyAsync(node, h->hb.link_node, sizeof(int) * k, cudaMemcpyDeviceToHost, g->stream), &h->err);
+  if (dir) CK(cudaMemcpyAsync(dir, h->hb.link_dir, k, cudaMemcpyDeviceToHost, g->stream), &h->err);
+  CK(cudaMemcpyAsync(c8.data(), h->hb.link_col, k, cudaMemcpyDeviceToHost, g->stream), &h->err);
+  CK(cudaStreamSynchronize(g->stream), &h->err);
+  if (colloid)
+    for (size_t i = 0; i < k; ++i) colloid[i] = c8[i];
+  return LC_OK;
+}
+
+int lc_lb_diagnostics(lc_lb* h, lc_diag* out) {
+  if (int rc = h_check(h)) return rc;
+  if (!out) return fail(&h->err, LC_ERR_ARG, "null output");
+  Group* g = h->g;
+  memset(out, 0, sizeof(*out));
+  long long nf = 0, nd = 0;
+  double sums[4];
+  int rc = count_fluid(g, h, &nf, &nd, sums);
+  if (rc) return rc;
+  out->n_fluid = nf;
+  out->n_defect = nd;
+  out->mass = (double)nf * h->hb.p.rho0 + sums[0];
+  for (int a = 0; a < 3; ++a) out->momentum[a] = sums[1 + a];
+  if (h->hb.p.lc_on) {
+    CK(launch_phase(g, 0, FORCE_FE, h->index), &h->err);
+    Phase& P = g->ph[0];
+    CK(launch_reduce(P.d_part, P.start[h->index], P.count[h->index], 1, 0u, g->d_red, g->stream), &h->err);
+    CK(cudaMemcpyAsync(g->h_red, g->d_red, sizeof(double), cudaMemcpyDeviceToHost, g->stream), &h->err);
+    CK(cudaStreamSynchronize(g->stream), &h->err);
+    out->free_energy = g->h_red[0];
+    double rms = 0, mx = 0;
+    if ((rc = box_residual(g, h->index, &rms, &mx, nf))) return rc;
+    out->resid_rms = rms;
+    out->resid_max = mx;
+  }
+  DevState st{};
+  CK(cudaMemcpyAsync(&st, h->hb.st, sizeof(st), cudaMemcpyDeviceToHost, g->stream), &h->err);
+  CK(cudaStreamSynchronize(g->stream), &h->err);
+  out->step = st.step;
+  if (!std::isfinite(out->mass) || !std::isfinite(out->free_energy))
+    return fail(&h->err, LC_ERR_NONFINITE, "non-finite diagnostics");
+  return LC_OK;
+}
+
+int lc_lb_profile(lc_lb* h, int nsteps, double ms_out[5]) {
+  if (int rc = h_check(h)) return rc;
+  if (!h->owns_group) return fail(&h->err, LC_ERR_STATE, "box of a batch: profile the batch");
+  if (nsteps < 1 || !ms_out) return fail(&h->err, LC_ERR_ARG, "bad profile arguments");
+  int rc = group_profile(h->g, nsteps, ms_out);
+  if (rc) h->err = h->g->err;
+  return rc;
+}
+
+int lc_lb_batch_profile(lc_lb_batch* b, int nsteps, double ms_out[5]) {
+  if (!b || nsteps < 1 || !ms_out) return fail(b ? &b->err : nullptr, LC_ERR_ARG, "bad profile arguments");
+  int rc = group_profile(b->g, nsteps, ms_out);
+  if (rc) b->err = b->g->err;
+  return rc;
+}
+
+const char* lc_lb_last_error(const lc_lb* h) {
+  if (!h) return g_err.c_str();
+  if (!h->err.empty()) return h->err.c_str();
+  return h->g ? h->g->err.c_str() : "";
+}
+
+// ---- batch ------------------------------------------------------------------
+int lc_lb_batch_create(int n, const lc_grid* grids, const lc_params* params, void* stream, lc_lb_batch** out) {
+  if (!out || n < 1 || !grids || !params) return fail(nullptr, LC_ERR_ARG, "bad batch arguments");
+  *out = nullptr;
+  std::string err;
+  for (int i = 0; i < n; ++i) {
+    int rc = check_params(grids + i, params + i, &err);
+    if (rc) return rc;
+    if (params[i].precision != params[0].precision) return fail(nullptr, LC_ERR_ARG, "mixed precision in a batch");
+  }
+  Group* g = new_group(params[0].precision, stream, n, &err);
+  if (!g) return LC_ERR_OOM;
+  int rc = LC_OK;
+  for (int i = 0; i < n && !rc; ++i) {
+    lc_lb* h = new lc_lb();
+    h->g = g;
+    h->index = i;
+    g->boxes.push_back(h);
+    rc = make_box(g, grids + i, params + i, h);
+    if (!rc) rc = rebuild_geometry(h);
+    if (rc) g_err = h->err;
+  }
+  for (int k = 0; k < 3 && !rc; ++k) rc = build_phase(g, k);
+  if (!rc) rc = build_chunks(g);
+  if (rc) {
+    free_group(g);
+    return rc;
+  }
+  CK(cudaStreamSynchronize(g->stream), nullptr);
+  lc_lb_batch* b = new lc_lb_batch();
+  b->g = g;
+  *out = b;
+  return LC_OK;
+}
+
+void lc_lb_batch_destroy(lc_lb_batch* b) {
+  if (!b) return;
+  free_group(b->g);
+  delete b;
+}
+
+int lc_lb_batch_box(lc_lb_batch* b, int i, lc_lb** box) {
+  if (!b || !box || i < 0 || i >= (int)b->g->boxes.size()) return fail(b ? &b->err : nullptr, LC_ERR_ARG, "no box %d", i);
+  *box = b->g->boxes[i];
+  return LC_OK;
+}
+
+int lc_lb_batch_step(lc_lb_batch* b, int nsteps) {
+  if (!b) return fail(nullptr, LC_ERR_ARG, "null batch");
+  int rc = group_step(b->g, nsteps);
+  if (rc) b->err = b->g->err;
+  return rc;
+}
+
+int lc_lb_batch_relax(lc_lb_batch* b, double tol, long long max_steps, int check_every, long long* steps_out,
+                      double* resid_out) {
+  if (!b || check_every < 1 || max_steps < 0) return fail(b ? &b->err : nullptr, LC_ERR_ARG, "bad relax arguments");
+  Group* g = b->g;
+  const int n = (int)g->boxes.size();
+  std::vector<long long> nf(n);
+  for (int i = 0; i < n; ++i) {
+    int rc = count_fluid(g, g->boxes[i], &nf[i], nullptr, nullptr);
+    if (rc) return rc;
+  }
+  std::vector<double> r(n, INFINITY);
+  long long done = 0;
+  while (done < max_steps) {
+    const int k = (int)std::min<long long>(check_every, max_steps - done);
+    int rc = group_step(g, k);
+    if (rc) {
+      b->err = g->err;
+      return rc;
+    }
+    done += k;
+    bool ok = true;
+    for (int i = 0; i < n; ++i) {
+      double mx;
+      if ((rc = box_residual(g, i, &r[i], &mx, nf[i]))) return rc;
+      if (!std::isfinite(r[i])) return fail(&b->err, LC_ERR_NONFINITE, "box %d residual not finite", i);
+      ok = ok && r[i] <= tol;
+    }
+    if (ok) break;
+  }
+  if (steps_out) *steps_out = done;
+  if (resid_out)
+    for (int i = 0; i < n; ++i) resid_out[i] = r[i];
+  return LC_OK;
+}
+
+const char* lc_lb_batch_last_error(const lc_lb_batch* b) {
+  if (!b) return g_err.c_str();
+  return b->err.empty() ? b->g->err.c_str() : b->err.c_str();
+}
+
+int lc_lb_autotune(const lc_grid* grid, int precision, void* stream, char* out_desc, size_t desc_len) {
+  lc_params p;
+  memset(&p, 0, sizeof(p));
+  p.rho0 = 1.0; p.tau = 2.5; p.A0 = 0.01; p.gamma = 3.0; p.K = 0.01; p.q0 = 0.0; p.xi = 0.7; p.Gamma = 0.5;
+  p.precision = precision; p.lc_enabled = 1; p.flow_enabled = 1;
+  lc_lb* h = nullptr;
+  int rc = lc_lb_create(grid, &p, stream, &h);
+  if (rc) return rc;
+  const double n[3] = {0.0, 0.0, 1.0};
+  lc_lb_init_uniaxial(h, n, 1e-3, 1);
+  std::string desc;
+  rc = autotune_group(h->g, &desc);
+  if (out_desc && desc_len) snprintf(out_desc, desc_len, "%s", desc.c_str());
+  if (rc) g_err = h->g->err;
+  lc_lb_destroy(h);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,46 @@
+// lclb_internal.h -- host-side interface between the C ABI (lclb_api.cu) and
+// the kernel launchers (lclb_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lclb_dev.cuh"
+
+namespace lclb {
+
+// mode bits
+constexpr int FORCE_ACC = 1;  // accumulate colloid LC force/torque
+constexpr int FORCE_FE = 2;   // write free-energy partials (one double per tile)
+constexpr int LB_MOM = 1;     // write mass/momentum partials (4 doubles per tile)
+constexpr int LC_RESID = 1;   // write residual partials (sum of squares, max; 2 doubles per tile)
+
+// export selectors (same values as LC_* in lc_lb.h)
+constexpr int EXP_Q = 0, EXP_U = 1, EXP_RHO = 2, EXP_F = 3, EXP_FORCE = 4, EXP_SOLID = 5;
+
+// One phase launch over a tile work list.
+struct Launch {
+  const DevBox* boxes;
+  const int4* tiles;  // (box, x0, y0, z0)
+  int ntiles;
+  int zc;             // tile depth in z
+  int ty;             // tile height in y (tile width in x is 32)
+  int grid;           // blocks (persistent: tiles are strided over blocks)
+  cudaStream_t stream;
+};
+
+cudaError_t launch_force(int prec, const Launch& L, int mode, double* part);
+cudaError_t launch_lb(int prec, const Launch& L, int mode, double* part);
+cudaError_t launch_lc(int prec, const Launch& L, int mode, double* part);
+cudaError_t launch_links(int prec, const DevBox* boxes, const int2* chunks, int nchunks, int grid, cudaStream_t s);
+cudaError_t launch_colloid(DevBox* boxes, int nboxes, cudaStream_t s);
+cudaError_t launch_geometry(DevBox* boxes, int b, int N, cudaStream_t s);
+cudaError_t launch_link_build(DevBox* boxes, int b, int N, int c, int* blocksum, int base, int* total,
+                              cudaStream_t s);
+cudaError_t launch_init_q(int prec, DevBox* boxes, int b, int N, int kind, const double* n, double amp,
+                          unsigned long long seed, cudaStream_t s);
+cudaError_t launch_set_field(int prec, DevBox* boxes, int b, int N, int which, const double* src, cudaStream_t s);
+cudaError_t launch_export(int prec, const DevBox* boxes, int b, int N, int which, double* out, cudaStream_t s);
+int diag_state_blocks(int N);
+cudaError_t launch_diag_state(int prec, const DevBox* boxes, int b, int N, double* part, cudaStream_t s);
+cudaError_t launch_reduce(const double* part, int rec0, int n, int w, unsigned maxmask, double* out, cudaStream_t s);
+
+}  // namespace lclb

@@ -1,0 +1,1024 @@
+// lclb_kernels.cu -- sm_103a kernels of one coupled step (Lintuvuori et al., Sec. 2.2):
+//   k_force   LC stress at fluid nodes, its face divergence (body force) and the
+//             colloid LC force/torque (Eqs. 4, 7); z-marching tiles with the
+//             stress of three planes in shared memory.
+//   k_lb      pull-scheme stream + BGK collide with Guo forcing, bounce-back on
+//             links inline (moving-surface term), writes df* and u.
+//   k_lc      Beris-Edwards update of Q (Eq. 2 with co-rotation and upwind
+//             advective face fluxes), residual partials.
+//   k_links   momentum exchange over the boundary-link list -> F_hyd, T_hyd.
+//   k_colloid colloid update and buffer-parity flip.
+// All step kernels walk a work list of (box, x0, y0, z0) tiles, so that one
+// launch serves one box or a batch of boxes of different sizes.
+#include <cstdio>
+
+#include "lclb_dev.cuh"
+#include "lclb_internal.h"
+
+namespace lclb {
+
+constexpr int TX = 32;
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block sum of NV doubles per thread; result valid in thread 0.  sred needs
+// 32*NV doubles.  Must be called by all threads of the block.
+template <int NV>
+__device__ void block_sum(double v[NV], double* sred, bool is_max_last = false) {
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int lane = tid & 31, wid = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = (is_max_last && k == NV - 1) ? warp_max(v[k]) : warp_sum(v[k]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sred[k * 32 + wid] = v[k];
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = lane < nw ? sred[k * 32 + lane] : 0.0;
+      v[k] = (is_max_last && k == NV - 1) ? warp_max(t) : warp_sum(t);
+    }
+  }
+  __syncthreads();
+}
+
+// Add per-lane contributions v[0..5] (for colloid id c, -1: none) into
+// acc[off..off+5] of each colloid with one FP64 atomic per (warp, colloid,
+// component).  Must be called by all 32 lanes of a converged warp.
+__device__ __forceinline__ void warp_flush_colloid(DevColloid* col, int c, double v[6], int off) {
+  unsigned pend = __ballot_sync(0xffffffffu, c >= 0);
+  const int lane = threadIdx.x & 31;
+  while (pend) {
+    const int leader = __ffs(pend) - 1;
+    const int cc = __shfl_sync(0xffffffffu, c, leader);
+    const bool mine = (c == cc);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const double t = warp_sum(mine ? v[k] : 0.0);
+      if (lane == leader && t != 0.0) atomicAdd(&col[cc].acc[off + k], t);
+    }
+    if (mine) c = -1;
+    pend = __ballot_sync(0xffffffffu, c >= 0);
+  }
+}
+
+__device__ __forceinline__ void load_box(DevBox& sb, const DevBox* boxes, int b) {
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) sb = boxes[b];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// k_force
+// ---------------------------------------------------------------------------
+// Shared memory: P of three z planes over the tile plus a one-node halo,
+// [3][9][(TX+2)(TY+2)] in T, then one flag byte per position.
+template <typename T, int TY>
+__global__ void __launch_bounds__(TX * TY) k_force(const DevBox* __restrict__ boxes, const int4* __restrict__ tiles,
+                                                   int ntiles, int zc, int mode, double* __restrict__ part) {
+  constexpr int HX = TX + 2, HY = TY + 2, HP = HX * HY, NT = TX * TY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sP = reinterpret_cast<T*>(smem_raw);
+  uint8_t* sFl = smem_raw + sizeof(T) * 27 * HP;
+  __shared__ DevBox B;
+  __shared__ double sred[32 * 1];
+  const int tid = threadIdx.x + TX * threadIdx.y;
+
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int4 td = tiles[t];
+    load_box(B, boxes, td.x);
+    if (!B.p.lc_on) continue;
+    const PhysT<T>& PP = phys<T>(B);
+    int my_c = -1;  // colloid whose LC force this thread is accumulating
+    double my_acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const T* __restrict__ Q = static_cast<const T*>(B.Q[B.st->qpar]);
+    T* __restrict__ Fout = static_cast<T*>(B.F);
+    const int x0 = td.y, y0 = td.z, z0 = td.w;
+    const int nx = B.nx, ny = B.ny, nz = B.nz, N = B.N;
+    const int vx = min(TX, nx - x0), vy = min(TY, ny - y0);
+    const int zend = min(z0 + zc, nz);
+    double fe_acc = 0.0;
+    __syncthreads();
+
+    for (int k = z0 - 1; k <= zend; ++k) {
+      const int slot = (k - z0 + 1) % 3;
+      const bool wallplane = B.wall_z && (k < 0 || k >= nz);
+      const int kk = B.wall_z ? k : wrapn(k, nz);
+      for (int pidx = tid; pidx < HP; pidx += NT) {
+        const int hx = pidx % HX, hy = pidx / HX;
+        if (hx > vx + 1 || hy > vy + 1) continue;
+        uint8_t flag = WALLFLAG;
+        if (!wallplane) {
+          const int gx = wrapn(x0 - 1 + hx, nx), gy = wrapn(y0 - 1 + hy, ny);
+          const int i = gx + nx * (gy + ny * kk);
+          const uint8_t m = B.mask[i];
+          flag = m & IDMASK;
+          if (flag == 0) {
+            const bool interior = (mode & FORCE_FE) && hx >= 1 && hx <= vx && hy >= 1 && hy <= vy && k >= z0 &&
+                                  k < zend;
+            T qi[5], qn[6][5], dq[3][5], lap[5], h[5], p[9];
+            double surf = 0.0;
+            gather_q(B, Q, gx, gy, kk, i, m, qi, qn, interior ? &surf : nullptr);
+            derivatives(qi, qn, dq, lap);
+            molecular_field(PP, qi, dq, lap, h);
+            const T fp = free_energy_density(PP, qi, dq);
+            stress(PP, qi, dq, h, fp, p);
+#pragma unroll
+            for (int c = 0; c < 9; ++c) sP[(slot * 9 + c) * HP + pidx] = p[c];
+            if (interior) fe_acc += (double)fp + surf;
+          }
+        }
+        sFl[slot * HP + pidx] = flag;
+      }
+      __syncthreads();
+      if (k >= z0 + 1) {
+        const int kc = k - 1;
+        const int sm = (k - z0 - 1) % 3, s0 = (k - z0) % 3, sp = slot;
+        const int tx = threadIdx.x, ty = threadIdx.y;
+        if (tx < vx && ty < vy) {
+          const int pc = (tx + 1) + HX * (ty + 1);
+          if (sFl[s0 * HP + pc] == 0) {
+            const int x = x0 + tx, y = y0 + ty;
+            T Fv[3] = {T(0), T(0), T(0)};
+            const int nslot[6] = {s0, s0, s0, s0, sp, sm};
+            const int npos[6] = {pc + 1, pc - 1, pc + HX, pc - HX, pc, pc};
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+              const int ax = d >> 1;
+              const T sgn = (d & 1) ? T(-1) : T(1);
+              const uint8_t fj = sFl[nslot[d] * HP + npos[d]];
+              T pcv[3];
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                pcv[a] = sP[(s0 * 9 + 3 * a + ax) * HP + pc];
+                const T face = (fj == 0) ? T(0.5) * (pcv[a] + sP[(nslot[d] * 9 + 3 * a + ax) * HP + npos[d]]) : pcv[a];
+                Fv[a] += sgn * face;
+              }
+              if ((mode & FORCE_ACC) && fj != 0 && fj != WALLFLAG) {
+                const int c = fj - 1;
+                const DevColloid& C = B.col[c];
+                double ff[3] = {-(double)sgn * (double)pcv[0], -(double)sgn * (double)pcv[1],
+                                -(double)sgn * (double)pcv[2]};
+                double r[3];
+                const double hx2 = 0.5 * (double)(ax == 0 ? sgn : 0), hy2 = 0.5 * (double)(ax == 1 ? sgn : 0),
+                             hz2 = 0.5 * (double)(ax == 2 ? sgn : 0);
+                disp(B, (double)x + hx2, (double)y + hy2, (double)kc + hz2, C.X, r);
+                double tq[3] = {r[1] * ff[2] - r[2] * ff[1], r[2] * ff[0] - r[0] * ff[2], r[0] * ff[1] - r[1] * ff[0]};
+                if (my_c >= 0 && my_c != c) {  // a second colloid at this node: flush the first directly
+                  for (int a = 0; a < 6; ++a) {
+                    atomicAdd(&B.col[my_c].acc[6 + a], my_acc[a]);
+                    my_acc[a] = 0.0;
+                  }
+                }
+                my_c = c;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                  my_acc[a] += ff[a];
+                  my_acc[3 + a] += tq[a];
+                }
+              }
+            }
+            const int ic = x + nx * (y + ny * kc);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Fout[(size_t)a * N + ic] = Fv[a];
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (mode & FORCE_ACC) warp_flush_colloid(B.col, my_c, my_acc, 6);
+    if (mode & FORCE_FE) {
+      double v[1] = {fe_acc};
+      block_sum<1>(v, sred);
+      if (tid == 0) part[t] = v[0];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pull with bounce-back (shared by k_lb and the export/diagnostic kernels)
+// ---------------------------------------------------------------------------
+// Gathers the pre-collision deviations df_q(r) = df*_q(r - c_q) for fluid
+// node r, or, when r - c_q is solid (colloid) or beyond a wall, the bounced
+// population df*_{-q}(r) + 6 w_q rho0 (c_q . u_b) with u_b the rigid velocity
+// at the link midpoint r - c_q/2 of the state that produced df* (Vb, Wb, Xb).
+template <typename T>
+__device__ __forceinline__ void pull(const DevBox& B, const T* __restrict__ fin, int x, int y, int z, int i, uint8_t m,
+                                     bool pre, T df[NQ]) {
+  const int N = B.N;
+  if (pre) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) df[q] = ldg(fin + (size_t)q * N + i);
+    return;
+  }
+  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x + 1 == nx ? 0 : x + 1};
+  const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y + 1 == ny ? 0 : y + 1};
+  int zs[3];
+  if (B.wall_z) {
+    zs[0] = z - 1; zs[1] = z; zs[2] = z + 1;
+  } else {
+    zs[0] = z == 0 ? nz - 1 : z - 1; zs[1] = z; zs[2] = z + 1 == nz ? 0 : z + 1;
+  }
+  if (!(m & NEAR)) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int s = xs[1 - cx(q)] + nx * (ys[1 - cy(q)] + ny * zs[1 - cz(q)]);
+      df[q] = ldg(fin + (size_t)q * N + s);
+    }
+    return;
+  }
+  const T rho0 = phys<T>(B).rho0;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int zsrc = zs[1 - cz(q)];
+    int s = -1;
+    uint8_t ms = WALLFLAG;
+    if (zsrc >= 0 && zsrc < nz) {
+      s = xs[1 - cx(q)] + nx * (ys[1 - cy(q)] + ny * zsrc);
+      ms = B.mask[s] & IDMASK;
+    }
+    if (ms == 0) {
+      df[q] = ldg(fin + (size_t)q * N + s);
+    } else {
+      T corr = T(0);
+      if (ms != WALLFLAG) {
+        const DevColloid& C = B.col[ms - 1];
+        T ub[3];
+        rigid_velocity_t<T>(B, T(x) - T(0.5 * cx(q)), T(y) - T(0.5 * cy(q)), T(z) - T(0.5 * cz(q)), C.Xb, C.Vb, C.Wb,
+                            ub);
+        const T cub = T(cx(q)) * ub[0] + T(cy(q)) * ub[1] + T(cz(q)) * ub[2];
+        corr = T(6.0 * wq(q)) * rho0 * cub;
+      }
+      df[q] = ldg(fin + (size_t)opp(q) * N + i) + corr;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_lb
+// ---------------------------------------------------------------------------
+template <typename T, int TY>
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * TY)) k_lb(const DevBox* __restrict__ boxes, const int4* __restrict__ tiles,
+                                                int ntiles, int zc, int mode, double* __restrict__ part) {
+  __shared__ DevBox B;
+  __shared__ double sred[32 * 4];
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int4 td = tiles[t];
+    load_box(B, boxes, td.x);
+    if (!B.p.flow_on) continue;
+    const int fpar = B.st->fpar;
+    const bool pre = B.st->pre_valid != 0;
+    const T* __restrict__ fin = static_cast<const T*>(B.f[fpar]);
+    T* __restrict__ fout = static_cast<T*>(B.f[fpar ^ 1]);
+    const T* __restrict__ Fb = static_cast<const T*>(B.F);
+    T* __restrict__ ub = static_cast<T*>(B.u);
+    const int nx = B.nx, ny = B.ny, N = B.N;
+    const int x = td.y + threadIdx.x, y = td.z + threadIdx.y;
+    const int zend = min(td.w + zc, B.nz);
+    const bool valid = x < nx && y < ny;
+    const PhysT<T>& PP = phys<T>(B);
+    const T rho0 = PP.rho0, omega = PP.omega, pref = PP.pref;
+    const T gx = PP.g[0], gy = PP.g[1], gz = PP.g[2];
+    const bool lc = B.p.lc_on != 0;
+    double dsum[4] = {0.0, 0.0, 0.0, 0.0};
+    if (valid) {
+      for (int z = td.w; z < zend; ++z) {
+        const int i = x + nx * (y + ny * z);
+        const uint8_t m = B.mask[i];
+        if (m & IDMASK) {
+          const DevColloid& C = B.col[(m & IDMASK) - 1];
+          T ur[3];
+          rigid_velocity_t<T>(B, T(x), T(y), T(z), C.X, C.V, C.W, ur);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) ub[(size_t)a * N + i] = ur[a];
+          continue;
+        }
+        T df[NQ];
+        pull(B, fin, x, y, z, i, m, pre, df);
+        T drho = T(0), mx = T(0), my = T(0), mz = T(0);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          drho += df[q];
+          if (cx(q)) mx += cx(q) > 0 ? df[q] : -df[q];
+          if (cy(q)) my += cy(q) > 0 ? df[q] : -df[q];
+          if (cz(q)) mz += cz(q) > 0 ? df[q] : -df[q];
+        }
+        T Fx = gx, Fy = gy, Fz = gz;
+        if (lc) {
+          Fx += Fb[i];
+          Fy += Fb[(size_t)N + i];
+          Fz += Fb[(size_t)2 * N + i];
+        }
+        const T rho = rho0 + drho;
+        const T inv = T(1) / rho;
+        const T ux = (mx + T(0.5) * Fx) * inv, uy = (my + T(0.5) * Fy) * inv, uz = (mz + T(0.5) * Fz) * inv;
+        const T usq = ux * ux + uy * uy + uz * uz;
+        const T uF = ux * Fx + uy * Fy + uz * Fz;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const T w = T(wq(q));
+          const T cu = T(cx(q)) * ux + T(cy(q)) * uy + T(cz(q)) * uz;
+          const T cF = T(cx(q)) * Fx + T(cy(q)) * Fy + T(cz(q)) * Fz;
+          const T eq = w * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
+          const T src = pref * w * (T(3) * (cF - uF) + T(9) * cu * cF);
+          fout[(size_t)q * N + i] = df[q] - omega * (df[q] - eq) + src;
+        }
+        ub[i] = ux;
+        ub[(size_t)N + i] = uy;
+        ub[(size_t)2 * N + i] = uz;
+        if (mode & LB_MOM) {
+          dsum[0] += (double)drho;
+          dsum[1] += (double)mx;
+          dsum[2] += (double)my;
+          dsum[3] += (double)mz;
+        }
+      }
+    }
+    if (mode & LB_MOM) {
+      block_sum<4>(dsum, sred);
+      if (tid == 0)
+        for (int k = 0; k < 4; ++k) part[4 * t + k] = dsum[k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_lc: Beris-Edwards update
+// ---------------------------------------------------------------------------
+template <typename T, int TY>
+__global__ void __launch_bounds__(TX * TY) k_lc(const DevBox* __restrict__ boxes, const int4* __restrict__ tiles,
+                                                int ntiles, int zc, int mode, double* __restrict__ part) {
+  __shared__ DevBox B;
+  __shared__ double sred[32 * 2];
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int4 td = tiles[t];
+    load_box(B, boxes, td.x);
+    if (!B.p.lc_on) continue;
+    const int qpar = B.st->qpar;
+    const T* __restrict__ Q = static_cast<const T*>(B.Q[qpar]);
+    T* __restrict__ Qo = static_cast<T*>(B.Q[qpar ^ 1]);
+    const T* __restrict__ U = static_cast<const T*>(B.u);
+    const int nx = B.nx, ny = B.ny, N = B.N;
+    const int x = td.y + threadIdx.x, y = td.z + threadIdx.y;
+    const int zend = min(td.w + zc, B.nz);
+    const bool valid = x < nx && y < ny;
+    const PhysT<T>& PP = phys<T>(B);
+    const T Gam = PP.Gamma, xi = PP.xi;
+    T rsum = T(0), rmax = T(0);  // per-thread residual (sum of squares, max), in T
+    if (valid) {
+      for (int z = td.w; z < zend; ++z) {
+        const int i = x + nx * (y + ny * z);
+        const uint8_t m = B.mask[i];
+        if (m & IDMASK) continue;
+        T qi[5], qn[6][5], dq[3][5], lap[5], h[5];
+        gather_q(B, Q, x, y, z, i, m, qi, qn, nullptr);
+        derivatives(qi, qn, dq, lap);
+        molecular_field(PP, qi, dq, lap, h);
+        int nb[6], zz[2];
+        face_neighbours(B, x, y, z, nb, zz);
+        T ui[3], un[6][3];
+        bool fl[6];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ui[a] = ldg(U + (size_t)a * N + i);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+          const int j = nb[d];
+          fl[d] = j >= 0 && (!(m & NEAR) || (B.mask[j] & IDMASK) == 0);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) un[d][a] = j >= 0 ? ldg(U + (size_t)a * N + j) : T(0);
+        }
+        // velocity gradient W_ab = d_b u_a
+        T W[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) W[a][b] = T(0.5) * (un[2 * b][a] - un[2 * b + 1][a]);
+        // advective fluxes through the six faces (zero across solid faces)
+        T adv[5] = {T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+          if (!fl[d]) continue;
+          const int ax = d >> 1;
+          const T uf = T(0.5) * (ui[ax] + un[d][ax]);
+          const bool plus = (d & 1) == 0;
+          // + face: upwind is i when uf > 0; - face: upwind is the neighbour when uf > 0
+          const bool take_i = plus ? (uf > T(0)) : !(uf > T(0));
+#pragma unroll
+          for (int k = 0; k < 5; ++k) {
+            const T fl_ = uf * (take_i ? qi[k] : qn[d][k]);
+            adv[k] += plus ? fl_ : -fl_;
+          }
+        }
+        // co-rotation S = xi (D Qt + Qt D) + (Om Q - Q Om) - 2 xi Qt Tr(Q W), Qt = Q + I/3
+        T D[3][3], Om[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            D[a][b] = T(0.5) * (W[a][b] + W[b][a]);
+            Om[a][b] = T(0.5) * (W[a][b] - W[b][a]);
+          }
+        T trQW = T(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) trQW += qab(qi, a, b) * D[a][b];
+        T dQ[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            T s = T(0);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              s += xi * (D[a][c] * qab(qi, c, b) + qab(qi, a, c) * D[c][b]) + Om[a][c] * qab(qi, c, b) -
+                   qab(qi, a, c) * Om[c][b];
+            s += xi * T(2) / T(3) * D[a][b];
+            s -= T(2) * xi * (qab(qi, a, b) + (a == b ? T(1) / T(3) : T(0))) * trQW;
+            dQ[a][b] = s;
+          }
+        const T tr = dQ[0][0] + dQ[1][1] + dQ[2][2];
+        const int ia[5] = {0, 0, 0, 1, 1}, ib[5] = {0, 1, 2, 1, 2};
+        T d5[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          T v = Gam * h[k] + dQ[ia[k]][ib[k]] - adv[k];
+          if (ia[k] == ib[k]) v -= tr / T(3);
+          d5[k] = v;
+          Qo[(size_t)k * N + i] = qi[k] + v;
+        }
+        const T dzz = -d5[0] - d5[3];
+        rsum += d5[0] * d5[0] + d5[3] * d5[3] + dzz * dzz + T(2) * (d5[1] * d5[1] + d5[2] * d5[2] + d5[4] * d5[4]);
+        T mx = fabs(dzz);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) mx = fmax(mx, fabs(d5[k]));
+        rmax = fmax(rmax, mx);
+      }
+    }
+    if (mode & LC_RESID) {
+      double rs[2] = {(double)rsum, (double)rmax};
+      block_sum<2>(rs, sred, true);
+      if (tid == 0) {
+        part[2 * t] = rs[0];
+        part[2 * t + 1] = rs[1];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_links: momentum exchange on the boundary links
+// ---------------------------------------------------------------------------
+// Per link (fluid r, direction b into colloid c): dp = c_b (2 df*_b(r) -
+// 6 w_b rho0 c_b.u_b), u_b the rigid velocity at r + c_b/2; torque
+// (r + c_b/2 - X) x dp.  The constant w_b rho0 part of 2 f*_b sums to zero
+// over a closed surface and is left out.
+template <typename T>
+__global__ void __launch_bounds__(256) k_links(const DevBox* __restrict__ boxes, const int2* __restrict__ chunks,
+                                               int nchunks) {
+  __shared__ DevBox B;
+  const int tid = threadIdx.x;
+  for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int2 cd = chunks[ch];
+    load_box(B, boxes, cd.x);
+    if (!B.p.flow_on) continue;
+    const int nl = *B.nlinks;
+    const int l = cd.y + tid;
+    int my_c = -1;
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (l < nl && l < B.nlinks_cap) {
+      const int i = B.link_node[l];
+      const int q = B.link_dir[l];
+      const int c = B.link_col[l];
+      const T* fout = static_cast<const T*>(B.f[B.st->fpar ^ 1]);
+      const double dfq = (double)fout[(size_t)q * B.N + i];
+      const int x = i % B.nx, y = (i / B.nx) % B.ny, z = i / (B.nx * B.ny);
+      int qx = 0, qy = 0, qz = 0;
+      switch (q) {
+#define LCLB_CASE(k) case k: qx = cx(k); qy = cy(k); qz = cz(k); break;
+        LCLB_CASE(1) LCLB_CASE(2) LCLB_CASE(3) LCLB_CASE(4) LCLB_CASE(5) LCLB_CASE(6) LCLB_CASE(7) LCLB_CASE(8)
+        LCLB_CASE(9) LCLB_CASE(10) LCLB_CASE(11) LCLB_CASE(12) LCLB_CASE(13) LCLB_CASE(14) LCLB_CASE(15)
+        LCLB_CASE(16) LCLB_CASE(17) LCLB_CASE(18)
+#undef LCLB_CASE
+        default: break;
+      }
+      const double w = (q <= 6) ? 1.0 / 18.0 : 1.0 / 36.0;
+      const DevColloid& C = B.col[c];
+      double d[3], ubv[3];
+      disp(B, x + 0.5 * qx, y + 0.5 * qy, z + 0.5 * qz, C.X, d);
+      rigid_velocity(C.V, C.W, d, ubv);
+      const double corr = 6.0 * w * B.p.rho0 * (qx * ubv[0] + qy * ubv[1] + qz * ubv[2]);
+      const double mag = 2.0 * dfq - corr;
+      const double dp[3] = {qx * mag, qy * mag, qz * mag};
+      const double tq[3] = {d[1] * dp[2] - d[2] * dp[1], d[2] * dp[0] - d[0] * dp[2], d[0] * dp[1] - d[1] * dp[0]};
+      my_c = c;
+      for (int a = 0; a < 3; ++a) {
+        v[a] = dp[a];
+        v[3 + a] = tq[a];
+      }
+    }
+    warp_flush_colloid(B.col, my_c, v, 0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_colloid: explicit colloid update ("molecular dynamics-like step") and the
+// end-of-step parity flip.  One block per box, one thread per colloid.
+// ---------------------------------------------------------------------------
+__global__ void k_colloid(DevBox* __restrict__ boxes, int nboxes) {
+  const int b = blockIdx.x;
+  if (b >= nboxes) return;
+  DevBox& B = boxes[b];
+  for (int c = threadIdx.x; c < B.ncol; c += blockDim.x) {
+    DevColloid& C = B.col[c];
+    for (int a = 0; a < 3; ++a) {
+      C.Fh[a] = C.acc[a];
+      C.Th[a] = C.acc[3 + a];
+      C.Flc[a] = C.acc[6 + a];
+      C.Tlc[a] = C.acc[9 + a];
+    }
+    for (int a = 0; a < 3; ++a) {
+      C.imp[a] += C.Fh[a] + C.Flc[a];
+      C.aimp[a] += C.Th[a] + C.Tlc[a];
+      C.Xb[a] = C.X[a];
+      C.Vb[a] = C.V[a];
+      C.Wb[a] = C.W[a];
+    }
+    if (C.mobile) {
+      for (int a = 0; a < 3; ++a) {
+        C.V[a] += (C.Fh[a] + C.Flc[a] + C.Fext[a]) / C.M;
+        C.W[a] += (C.Th[a] + C.Tlc[a]) / C.I;
+      }
+      const int L[3] = {B.nx, B.ny, B.nz};
+      for (int a = 0; a < 3; ++a) {
+        C.X[a] += C.V[a];
+        if (a < 2 || !B.wall_z) {
+          if (C.X[a] >= L[a]) C.X[a] -= L[a];
+          if (C.X[a] < 0) C.X[a] += L[a];
+        }
+      }
+    }
+    for (int k = 0; k < 12; ++k) C.acc[k] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    DevState* st = B.st;
+    if (B.p.flow_on) {
+      st->fpar ^= 1;
+      st->pre_valid = 0;
+    }
+    if (B.p.lc_on) st->qpar ^= 1;
+    st->step += 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// geometry: solid mask, near flags, boundary links (cold path)
+// ---------------------------------------------------------------------------
+__global__ void k_mask(DevBox* __restrict__ boxes, int b) {
+  const DevBox& B = boxes[b];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B.N) return;
+  const int x = i % B.nx, y = (i / B.nx) % B.ny, z = i / (B.nx * B.ny);
+  uint8_t id = 0;
+  for (int c = 0; c < B.ncol; ++c)
+    if (inside_colloid(B, x, y, z, B.col[c])) {
+      if (id == 0) id = (uint8_t)(c + 1);
+      else atomicOr(&B.st->err, 4);  // overlap
+    }
+  B.mask[i] = id;
+}
+
+__global__ void k_near(DevBox* __restrict__ boxes, int b) {
+  const DevBox& B = boxes[b];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B.N) return;
+  uint8_t m = B.mask[i];
+  if (m & IDMASK) return;
+  const int x = i % B.nx, y = (i / B.nx) % B.ny, z = i / (B.nx * B.ny);
+  bool near = false;
+#pragma unroll
+  for (int q = 1; q < NQ; ++q) {
+    const int zz = z + cz(q);
+    if (B.wall_z && (zz < 0 || zz >= B.nz)) {
+      near = true;
+      continue;
+    }
+    const int j = wrap1(x + cx(q), B.nx) + B.nx * (wrap1(y + cy(q), B.ny) + B.ny * wrap1(zz, B.nz));
+    if (B.mask[j] & IDMASK) near = true;
+  }
+  B.mask[i] = near ? (uint8_t)(m | NEAR) : (uint8_t)(m & ~NEAR);
+}
+
+// Number of links from fluid node i into colloid c (bit q set in *bits).
+__device__ __forceinline__ int links_at(const DevBox& B, int i, int c, unsigned* bits) {
+  unsigned bm = 0;
+  if ((B.mask[i] & IDMASK) == 0 && (B.mask[i] & NEAR)) {
+    const int x = i % B.nx, y = (i / B.nx) % B.ny, z = i / (B.nx * B.ny);
+#pragma unroll
+    for (int q = 1; q < NQ; ++q) {
+      const int zz = z + cz(q);
+      if (B.wall_z && (zz < 0 || zz >= B.nz)) continue;
+      const int j = wrap1(x + cx(q), B.nx) + B.nx * (wrap1(y + cy(q), B.ny) + B.ny * wrap1(zz, B.nz));
+      if ((B.mask[j] & IDMASK) == (uint8_t)(c + 1)) bm |= 1u << q;
+    }
+  }
+  *bits = bm;
+  return __popc(bm);
+}
+
+__global__ void __launch_bounds__(256) k_link_count(const DevBox* __restrict__ boxes, int b, int c, int* blocksum) {
+  const DevBox& B = boxes[b];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned bits;
+  int n = i < B.N ? links_at(B, i, c, &bits) : 0;
+  __shared__ int s[8];
+  int v = n;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int k = 0; k < 8; ++k) t += s[k];
+    blocksum[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of n ints in one block (deterministic); total -> *total.
+__global__ void __launch_bounds__(1024) k_scan(int* a, int n, int base, int* total) {
+  __shared__ int s[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = base;
+  __syncthreads();
+  for (int off = 0; off < n; off += 1024) {
+    const int i = off + threadIdx.x;
+    const int v = i < n ? a[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+      int t = threadIdx.x >= d ? s[threadIdx.x - d] : 0;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < n) a[i] = carry + s[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += s[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(256) k_link_write(const DevBox* __restrict__ boxes, int b, int c,
+                                                    const int* blockoff) {
+  const DevBox& B = boxes[b];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned bits = 0;
+  const int n = i < B.N ? links_at(B, i, c, &bits) : 0;
+  __shared__ int s[256];
+  s[threadIdx.x] = n;
+  __syncthreads();
+  for (int d = 1; d < 256; d <<= 1) {
+    int t = threadIdx.x >= d ? s[threadIdx.x - d] : 0;
+    __syncthreads();
+    s[threadIdx.x] += t;
+    __syncthreads();
+  }
+  int pos = blockoff[blockIdx.x] + s[threadIdx.x] - n;
+  for (int q = 1; q < NQ; ++q)
+    if (bits & (1u << q)) {
+      if (pos < B.nlinks_cap) {
+        B.link_node[pos] = i;
+        B.link_dir[pos] = (int8_t)q;
+        B.link_col[pos] = (int8_t)c;
+      } else {
+        atomicOr(&B.st->err, 1);
+      }
+      ++pos;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// init, export, diagnostics (cold path)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64(uint64_t s) {
+  uint64_t z = s + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// kind 0: uniaxial along (n0,n1,n2); kind 1: helix along axis (int)n0.
+template <typename T>
+__global__ void k_init_q(DevBox* __restrict__ boxes, int b, int kind, double n0, double n1, double n2, double amp,
+                         unsigned long long seed) {
+  const DevBox& B = boxes[b];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B.N) return;
+  const int x = i % B.nx, y = (i / B.nx) % B.ny, z = i / (B.nx * B.ny);
+  double d[3];
+  if (kind == 0) {
+    const double nn = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(n0, n0), __dmul_rn(n1, n1)), __dmul_rn(n2, n2)));
+    d[0] = n0 / nn; d[1] = n1 / nn; d[2] = n2 / nn;
+  } else {
+    const int ax = (int)n0, bb = (ax + 1) % 3, cc = (ax + 2) % 3;
+    const int r[3] = {x, y, z};
+    const double ph = B.p.q0 * r[ax];
+    d[0] = d[1] = d[2] = 0.0;
+    d[bb] = cos(ph);
+    d[cc] = sin(ph);
+  }
+  // S0 (d_a d_b - delta_ab/3) with round-to-nearest operations only (no
+  // contraction), so FP64 storage agrees bit for bit with a plain C evaluation.
+  const double S0 = B.p.S0, third = 1.0 / 3.0;
+  const double v[5] = {__dmul_rn(S0, __dsub_rn(__dmul_rn(d[0], d[0]), third)), __dmul_rn(S0, __dmul_rn(d[0], d[1])),
+                       __dmul_rn(S0, __dmul_rn(d[0], d[2])), __dmul_rn(S0, __dsub_rn(__dmul_rn(d[1], d[1]), third)),
+                       __dmul_rn(S0, __dmul_rn(d[1], d[2]))};
+  T* Qa = static_cast<T*>(B.Q[0]);
+  T* Qb = static_cast<T*>(B.Q[1]);
+  for (int k = 0; k < 5; ++k) {
+    const uint64_t r = splitmix64((uint64_t)seed ^ (uint64_t)(5LL * i + k));
+    const double u = (double)(r >> 11) * (1.0 / 9007199254740992.0);
+    const double val = __dadd_rn(v[k], __dmul_rn(amp, __dsub_rn(2.0 * u, 1.0)));
+    Qa[(size_t)k * B.N + i] = T(val);
+    Qb[(size_t)k * B.N + i] = T(val);
+  }
+}
+
+// Convert FP64 input to storage: which 0 = Q (both buffers), 1 = f (pre-collision,
+// full f -> deviation into f[fpar], pre_valid set by the host).
+template <typename T>
+__global__ void k_set_field(DevBox* __restrict__ boxes, int b, int which, const double* __restrict__ src) {
+  const DevBox& B = boxes[b];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B.N) return;
+  if (which == 0) {
+    T* Qa = static_cast<T*>(B.Q[0]);
+    T* Qb = static_cast<T*>(B.Q[1]);
+    for (int k = 0; k < 5; ++k) {
+      const T v = T(src[(size_t)k * B.N + i]);
+      Qa[(size_t)k * B.N + i] = v;
+      Qb[(size_t)k * B.N + i] = v;
+    }
+  } else {
+    T* f = static_cast<T*>(B.f[B.st->fpar]);
+    for (int q = 0; q < NQ; ++q) f[(size_t)q * B.N + i] = T(src[(size_t)q * B.N + i] - wq(q) * B.p.rho0);
+  }
+}
+
+// Exports.  which: LC_Q, LC_F_PRE, LC_RHO, LC_U, LC_FORCE, LC_SOLID.
+template <typename T>
+__global__ void k_export(const DevBox* __restrict__ boxes, int b, int which, double* __restrict__ out) {
+  const DevBox& B = boxes[b];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B.N) return;
+  const int N = B.N;
+  const uint8_t m = B.mask[i];
+  const int x = i % B.nx, y = (i / B.nx) % B.ny, z = i / (B.nx * B.ny);
+  if (which == EXP_Q) {
+    const T* Q = static_cast<const T*>(B.Q[B.st->qpar]);
+    for (int k = 0; k < 5; ++k) out[(size_t)k * N + i] = (double)Q[(size_t)k * N + i];
+    return;
+  }
+  if (which == EXP_SOLID) {
+    out[i] = (m & IDMASK) ? (double)((m & IDMASK) - 1) : -1.0;
+    return;
+  }
+  if (which == EXP_FORCE) {
+    const T* F = static_cast<const T*>(B.F);
+    for (int a = 0; a < 3; ++a) out[(size_t)a * N + i] = (m & IDMASK) || !B.p.lc_on ? 0.0 : (double)F[(size_t)a * N + i];
+    return;
+  }
+  if (m & IDMASK) {
+    if (which == EXP_F) {
+      for (int q = 0; q < NQ; ++q) out[(size_t)q * N + i] = 0.0;
+    } else if (which == EXP_RHO) {
+      out[i] = B.p.rho0;
+    } else {
+      const DevColloid& C = B.col[(m & IDMASK) - 1];
+      double d[3], ur[3];
+      disp(B, (double)x, (double)y, (double)z, C.X, d);
+      rigid_velocity(C.V, C.W, d, ur);
+      for (int a = 0; a < 3; ++a) out[(size_t)a * N + i] = ur[a];
+    }
+    return;
+  }
+  T df[NQ];
+  pull(B, static_cast<const T*>(B.f[B.st->fpar]), x, y, z, i, m, B.st->pre_valid != 0, df);
+  if (which == EXP_F) {
+    for (int q = 0; q < NQ; ++q) out[(size_t)q * N + i] = wq(q) * B.p.rho0 + (double)df[q];
+    return;
+  }
+  double drho = 0.0, mm[3] = {0.0, 0.0, 0.0};
+  for (int q = 0; q < NQ; ++q) {
+    drho += (double)df[q];
+    mm[0] += cx(q) * (double)df[q];
+    mm[1] += cy(q) * (double)df[q];
+    mm[2] += cz(q) * (double)df[q];
+  }
+  const double rho = B.p.rho0 + drho;
+  if (which == EXP_RHO) {
+    out[i] = rho;
+    return;
+  }
+  const T* F = static_cast<const T*>(B.F);
+  for (int a = 0; a < 3; ++a) {
+    const double Fa = (B.p.lc_on ? (double)F[(size_t)a * N + i] : 0.0) + B.p.g[a];
+    out[(size_t)a * N + i] = (mm[a] + 0.5 * Fa) / rho;
+  }
+}
+
+// Diagnostics per block: [0] sum(df), [1..3] sum(df c), [4] fluid nodes,
+// [5] defect nodes (3/2 lambda_max(Q) < 0.435).
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag_state(const DevBox* __restrict__ boxes, int b, double* __restrict__ part) {
+  const DevBox& B = boxes[b];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  __shared__ double sred[32 * 6];
+  if (i < B.N) {
+    const uint8_t m = B.mask[i];
+    if (!(m & IDMASK)) {
+      const int x = i % B.nx, y = (i / B.nx) % B.ny, z = i / (B.nx * B.ny);
+      T df[NQ];
+      pull(B, static_cast<const T*>(B.f[B.st->fpar]), x, y, z, i, m, B.st->pre_valid != 0, df);
+      for (int q = 0; q < NQ; ++q) {
+        v[0] += (double)df[q];
+        v[1] += cx(q) * (double)df[q];
+        v[2] += cy(q) * (double)df[q];
+        v[3] += cz(q) * (double)df[q];
+      }
+      v[4] = 1.0;
+      const T* Q = static_cast<const T*>(B.Q[B.st->qpar]);
+      double q[5];
+      for (int k = 0; k < 5; ++k) q[k] = (double)Q[(size_t)k * B.N + i];
+      // largest eigenvalue of the traceless symmetric Q (closed form, as in principal_dir)
+      double a00 = q[0], a01 = q[1], a02 = q[2], a11 = q[3], a12 = q[4], a22 = -q[0] - q[3];
+      double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+      double p2 = a00 * a00 + a11 * a11 + a22 * a22 + 2.0 * p1;
+      double lam = 0.0;
+      if (p2 > 0.0) {
+        double p = sqrt(p2 / 6.0);
+        double b00 = a00 / p, b01 = a01 / p, b02 = a02 / p, b11 = a11 / p, b12 = a12 / p, b22 = a22 / p;
+        double det = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
+        double r = fmin(1.0, fmax(-1.0, det / 2.0));
+        lam = 2.0 * p * cos(acos(r) / 3.0);
+      }
+      v[5] = (1.5 * lam < 0.435) ? 1.0 : 0.0;
+    }
+  }
+  block_sum<6>(v, sred);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 6; ++k) part[6 * blockIdx.x + k] = v[k];
+}
+
+// Deterministic sum of n records of width w (column k) starting at rec0;
+// out[k] = sum, or max for columns flagged in maxmask.
+__global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ part, int rec0, int n, int w,
+                                                unsigned maxmask, double* __restrict__ out) {
+  __shared__ double s[256];
+  for (int k = 0; k < w; ++k) {
+    const bool ismax = (maxmask >> k) & 1u;
+    double v = 0.0;
+    for (int r = threadIdx.x; r < n; r += 256) {
+      const double x = part[(size_t)(rec0 + r) * w + k];
+      v = ismax ? fmax(v, x) : v + x;
+    }
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int d = 128; d > 0; d >>= 1) {
+      if (threadIdx.x < d) s[threadIdx.x] = ismax ? fmax(s[threadIdx.x], s[threadIdx.x + d]) : s[threadIdx.x] + s[threadIdx.x + d];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = s[0];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <typename T, int TY>
+static cudaError_t launch_force_t(const Launch& L, int mode, double* part) {
+  constexpr int HP = (TX + 2) * (TY + 2);
+  const size_t smem = sizeof(T) * 27 * HP + 3 * HP;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_force<T, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_force<T, TY><<<L.grid, dim3(TX, TY), smem, L.stream>>>(L.boxes, L.tiles, L.ntiles, L.zc, mode, part);
+  return cudaGetLastError();
+}
+
+template <typename T, int TY>
+static cudaError_t launch_lb_t(const Launch& L, int mode, double* part) {
+  k_lb<T, TY><<<L.grid, dim3(TX, TY), 0, L.stream>>>(L.boxes, L.tiles, L.ntiles, L.zc, mode, part);
+  return cudaGetLastError();
+}
+
+template <typename T, int TY>
+static cudaError_t launch_lc_t(const Launch& L, int mode, double* part) {
+  k_lc<T, TY><<<L.grid, dim3(TX, TY), 0, L.stream>>>(L.boxes, L.tiles, L.ntiles, L.zc, mode, part);
+  return cudaGetLastError();
+}
+
+#define LCLB_DISPATCH_TY(FN, T)                      \
+  switch (L.ty) {                                    \
+    case 2: return FN<T, 2>(L, mode, part);          \
+    case 4: return FN<T, 4>(L, mode, part);          \
+    case 8: return FN<T, 8>(L, mode, part);          \
+    default: return cudaErrorInvalidValue;           \
+  }
+
+cudaError_t launch_force(int prec, const Launch& L, int mode, double* part) {
+  if (prec == 0) { LCLB_DISPATCH_TY(launch_force_t, float) }
+  LCLB_DISPATCH_TY(launch_force_t, double)
+}
+cudaError_t launch_lb(int prec, const Launch& L, int mode, double* part) {
+  if (prec == 0) { LCLB_DISPATCH_TY(launch_lb_t, float) }
+  LCLB_DISPATCH_TY(launch_lb_t, double)
+}
+cudaError_t launch_lc(int prec, const Launch& L, int mode, double* part) {
+  if (prec == 0) { LCLB_DISPATCH_TY(launch_lc_t, float) }
+  LCLB_DISPATCH_TY(launch_lc_t, double)
+}
+
+cudaError_t launch_links(int prec, const DevBox* boxes, const int2* chunks, int nchunks, int grid, cudaStream_t s) {
+  if (nchunks <= 0) return cudaSuccess;
+  if (prec == 0) k_links<float><<<grid, 256, 0, s>>>(boxes, chunks, nchunks);
+  else k_links<double><<<grid, 256, 0, s>>>(boxes, chunks, nchunks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colloid(DevBox* boxes, int nboxes, cudaStream_t s) {
+  k_colloid<<<nboxes, 128, 0, s>>>(boxes, nboxes);
+  return cudaGetLastError();
+}
+
+static inline int nblk(int N, int bs) { return (N + bs - 1) / bs; }
+
+cudaError_t launch_geometry(DevBox* boxes, int b, int N, cudaStream_t s) {
+  k_mask<<<nblk(N, 256), 256, 0, s>>>(boxes, b);
+  k_near<<<nblk(N, 256), 256, 0, s>>>(boxes, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_link_build(DevBox* boxes, int b, int N, int c, int* blocksum, int base, int* total,
+                              cudaStream_t s) {
+  const int nb = nblk(N, 256);
+  k_link_count<<<nb, 256, 0, s>>>(boxes, b, c, blocksum);
+  k_scan<<<1, 1024, 0, s>>>(blocksum, nb, base, total);
+  k_link_write<<<nb, 256, 0, s>>>(boxes, b, c, blocksum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_q(int prec, DevBox* boxes, int b, int N, int kind, const double* n, double amp,
+                          unsigned long long seed, cudaStream_t s) {
+  if (prec == 0) k_init_q<float><<<nblk(N, 256), 256, 0, s>>>(boxes, b, kind, n[0], n[1], n[2], amp, seed);
+  else k_init_q<double><<<nblk(N, 256), 256, 0, s>>>(boxes, b, kind, n[0], n[1], n[2], amp, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_field(int prec, DevBox* boxes, int b, int N, int which, const double* src, cudaStream_t s) {
+  if (prec == 0) k_set_field<float><<<nblk(N, 256), 256, 0, s>>>(boxes, b, which, src);
+  else k_set_field<double><<<nblk(N, 256), 256, 0, s>>>(boxes, b, which, src);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export(int prec, const DevBox* boxes, int b, int N, int which, double* out, cudaStream_t s) {
+  if (prec == 0) k_export<float><<<nblk(N, 256), 256, 0, s>>>(boxes, b, which, out);
+  else k_export<double><<<nblk(N, 256), 256, 0, s>>>(boxes, b, which, out);
+  return cudaGetLastError();
+}
+
+int diag_state_blocks(int N) { return nblk(N, 256); }
+
+cudaError_t launch_diag_state(int prec, const DevBox* boxes, int b, int N, double* part, cudaStream_t s) {
+  if (prec == 0) k_diag_state<float><<<nblk(N, 256), 256, 0, s>>>(boxes, b, part);
+  else k_diag_state<double><<<nblk(N, 256), 256, 0, s>>>(boxes, b, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const double* part, int rec0, int n, int w, unsigned maxmask, double* out, cudaStream_t s) {
+  k_reduce<<<1, 256, 0, s>>>(part, rec0, n, w, maxmask, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lclb

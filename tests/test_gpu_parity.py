@@ -1,0 +1,324 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (max over fluid nodes after the run): |dQ| <= 1e-5 and |du| <= 1e-6
+in FP32 storage; colloid force relative error <= 1e-4; boundary links and the
+solid set bit-exact.  The FP64 path is held to 1e-10.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+# Q, u, f: max abs difference over fluid nodes.  F: relative error of the
+# colloid's total force and torque (hydrodynamic + LC); Fpart: of each part;
+# Fabs: absolute floor for quantities that are round-off noise around zero.
+TOL32 = dict(Q=1e-5, u=1e-6, f=1e-6, F=1e-4, Fpart=1e-3, Fabs=1e-10)
+TOL64 = dict(Q=1e-10, u=1e-12, f=1e-12, F=1e-9, Fpart=1e-8, Fabs=1e-14)
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1102_2193_gb300 as P
+    P.lib()
+    return P
+
+
+def make_pair(P, L, prm, prec, wall_z=False, colloids=(), init=("uniaxial", (0, 0, 1), 1e-3, 1), threads=8):
+    g = P.Solver(*L, wall_z=wall_z, precision=prec, **prm)
+    o = oracle.Oracle(*L, wall_z=wall_z, threads=threads, **prm)
+    kind = init[0]
+    if kind == "uniaxial":
+        g.init_uniaxial(init[1], amp=init[2], seed=init[3])
+        o.init_uniaxial(init[1], amp=init[2], seed=init[3])
+    elif kind == "helix":
+        g.init_helix(init[1], amp=init[2], seed=init[3])
+        o.init_helix(init[1], amp=init[2], seed=init[3])
+    for c in colloids:
+        g.add_colloid(c["X"], c["a0"], c.get("anchoring", 0), c.get("w", float("inf")), c.get("mobile", False),
+                      c.get("F_ext"))
+        o.add_colloid(c["X"], c["a0"], c.get("anchoring", 0), c.get("w", float("inf")), c.get("mobile", False),
+                      c.get("F_ext"))
+    return g, o
+
+
+def _vec_err(a, b, rtol, atol):
+    d = np.linalg.norm(np.asarray(a) - np.asarray(b))
+    return d <= rtol * np.linalg.norm(b) + atol, d, np.linalg.norm(b)
+
+
+def compare(g, o, tol, ncol=0, report=None, radii=None):
+    fl = o.get_solid() < 0
+    assert (g.get_solid() == o.get_solid()).all()
+    dQ = np.abs(g.get_Q() - o.get_Q())[:, fl].max()
+    rg, ug = g.get_rho_u()
+    ro, uo = o.get_rho_u()
+    du = np.abs(ug - uo)[:, fl].max()
+    df = np.abs(g.get_f() - o.get_f())[:, fl].max()
+    if report is not None:
+        report.update(dQ=dQ, du=du, df=df)
+    assert dQ <= tol["Q"], f"max|dQ| = {dQ:.3e}"
+    assert du <= tol["u"], f"max|du| = {du:.3e}"
+    assert df <= tol["f"], f"max|df| = {df:.3e}"
+    for c in range(ncol):
+        cg, co = g.colloid(c), o.colloid(c)
+        # torque errors are measured against the characteristic torque a0 (|F_hyd| + |F_lc|)
+        a0 = radii[c] if radii else 1.0
+        tscale = a0 * (np.linalg.norm(co["F_hyd"]) + np.linalg.norm(co["F_lc"]))
+        for name, keys, rt in (("force", ("F_hyd", "F_lc"), tol["F"]), ("torque", ("T_hyd", "T_lc"), tol["F"])):
+            extra = rt * tscale if name == "torque" else 0.0
+            ok, d, n = _vec_err(cg[keys[0]] + cg[keys[1]], co[keys[0]] + co[keys[1]], rt, tol["Fabs"] + extra)
+            if report is not None:
+                report[f"{name}{c}_rel"] = d / max(n, 1e-300)
+            assert ok, f"colloid {c} total {name}: |diff| {d:.3e} vs |ref| {n:.3e}"
+        for k in ("F_hyd", "F_lc", "T_hyd", "T_lc", "V", "X"):
+            extra = tol["Fpart"] * tscale if k[0] == "T" else 0.0
+            ok, d, n = _vec_err(cg[k], co[k], tol["Fpart"], tol["Fabs"] + extra)
+            assert ok, f"colloid {c} {k}: |diff| {d:.3e} vs |ref| {n:.3e} ({cg[k]} vs {co[k]})"
+    return dQ, du, df
+
+
+# ------------------------------------------------------------------ init --
+def test_init_bit_exact_fp64(P):
+    L = (13, 7, 5)
+    g, o = make_pair(P, L, synth.NEMATIC, P.LC_FP64, init=("uniaxial", (0, 0, 1), 1e-3, 12345))
+    assert (g.get_Q() == o.get_Q()).all()
+    g.init_uniaxial((0.3, -0.4, 0.8), amp=2e-3, seed=99)
+    o.init_uniaxial((0.3, -0.4, 0.8), amp=2e-3, seed=99)
+    assert (g.get_Q() == o.get_Q()).all()
+
+
+def test_init_rounds_to_fp32(P):
+    L = (9, 8, 7)
+    g, o = make_pair(P, L, synth.NEMATIC, P.LC_FP32, init=("uniaxial", (0, 0, 1), 1e-3, 77))
+    assert (g.get_Q() == o.get_Q().astype(np.float32).astype(np.float64)).all()
+    p = dict(synth.NEMATIC, q0=2 * math.pi / 7)
+    g2, o2 = make_pair(P, L, p, P.LC_FP64, init=("helix", 2, 1e-3, 5))
+    np.testing.assert_allclose(g2.get_Q(), o2.get_Q(), atol=1e-16)
+
+
+# ------------------------------------------------------------ geometry --
+@pytest.mark.parametrize("seed", range(6))
+def test_links_and_solid_bit_exact(P, seed):
+    rng = np.random.default_rng(300 + seed)
+    L = tuple(int(v) for v in rng.integers(6, 40, size=3))
+    X, a0 = synth.random_colloid(L, seed=400 + seed, rmin=1.5, rmax=min(L) / 2.5)
+    g, o = make_pair(P, L, synth.NEMATIC, P.LC_FP32, colloids=[dict(X=X, a0=a0)])
+    assert (g.get_solid() == o.get_solid()).all()
+    ng, dg, cg = g.links()
+    no, do, co = o.links()
+    assert len(ng) == len(no)
+    assert (ng == no).all() and (dg == do).all() and (cg == co).all()
+
+
+def test_links_two_colloids(P):
+    L = (40, 24, 20)
+    cols = [dict(X=(9.2, 11.7, 9.9), a0=4.3), dict(X=(29.6, 12.1, 10.4), a0=5.1)]
+    g, o = make_pair(P, L, synth.NEMATIC, P.LC_FP32, colloids=cols)
+    ng, dg, cg = g.links()
+    no, do, co = o.links()
+    assert (ng == no).all() and (dg == do).all() and (cg == co).all()
+
+
+def test_overlap_rejected(P):
+    g = P.Solver(16, 16, 16)
+    g.add_colloid((4, 4, 4), 3.0)
+    with pytest.raises(P.LcLbError) as e:
+        g.add_colloid((6, 4, 4), 3.0)
+    assert e.value.code == -4
+    g.add_colloid((12, 12, 12), 3.0)
+    assert len(g.links()[0]) == len(_links_oracle_two())
+
+
+def _links_oracle_two():
+    o = oracle.Oracle(16, 16, 16)
+    o.add_colloid((4, 4, 4), 3.0)
+    o.add_colloid((12, 12, 12), 3.0)
+    return o.links()[0]
+
+
+# ---------------------------------------------------- single-evaluation --
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_force_field_and_velocity_parity(P, prec):
+    L = (37, 29, 23)
+    p = dict(synth.NEMATIC, q0=2 * math.pi / 11, A0=0.05)
+    cols = [dict(X=(17.3, 14.1, 11.6), a0=5.2, anchoring=1, w=0.02), dict(X=(4.4, 5.5, 6.6), a0=3.1, w=float("inf"))]
+    g, o = make_pair(P, L, p, P.LC_FP32 if prec == "f32" else P.LC_FP64, colloids=cols,
+                     init=("uniaxial", (0.2, 0.5, 0.8), 5e-2, 3))
+    fl = o.get_solid() < 0
+    _, _, Fo, _ = o.lc_fields()
+    Fg = g.get_force_field()
+    scale = np.abs(Fo).max()
+    tol = 2e-5 if prec == "f32" else 1e-12
+    assert np.abs(Fg - Fo)[:, fl].max() <= tol * scale
+    _, ug = g.get_rho_u()
+    _, uo = o.get_rho_u()
+    assert np.abs(ug - uo)[:, fl].max() <= (1e-8 if prec == "f32" else 1e-15)
+
+
+# ------------------------------------------------------------- trajectories --
+def test_nematic32_fp64_200_steps(P):
+    """The 32^3 planar-anchored colloid run (FP64, 200 steps)."""
+    w = synth.workload("nematic32")
+    c = w["colloids"][0]
+    g, o = make_pair(P, w["grid"], w["params"], P.LC_FP64, colloids=[c],
+                     init=("uniaxial", w["init"]["n"], w["init"]["amp"], w["init"]["seed"]))
+    g.step(w["steps"])
+    o.step(w["steps"])
+    dQ, du, df = compare(g, o, TOL64, ncol=1, radii=[c["a0"]])
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_ragged_cholesteric_two_colloids(P, prec):
+    L = (37, 29, 23)
+    p = dict(synth.NEMATIC, q0=2 * math.pi / 16)
+    cols = [dict(X=(17.3, 14.1, 11.6), a0=5.2, anchoring=1, w=0.02), dict(X=(4.4, 5.5, 6.6), a0=3.1)]
+    g, o = make_pair(P, L, p, P.LC_FP32 if prec == "f32" else P.LC_FP64, colloids=cols,
+                     init=("helix", 2, 1e-2, 11))
+    g.step(60)
+    o.step(60)
+    compare(g, o, TOL32 if prec == "f32" else TOL64, ncol=2, radii=[5.2, 3.1])
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_walls_mobile_colloid(P, prec):
+    L = (24, 20, 18)
+    p = dict(synth.NEMATIC)
+    cols = [dict(X=(11.5, 9.5, 8.5), a0=4.0, anchoring=1, w=0.01, mobile=True, F_ext=(2e-4, 0.0, 1e-4))]
+    g, o = make_pair(P, L, p, P.LC_FP32 if prec == "f32" else P.LC_FP64, wall_z=True, colloids=cols,
+                     init=("uniaxial", (0, 0, 1), 1e-3, 2))
+    g.step(80)
+    o.step(80)
+    compare(g, o, TOL32 if prec == "f32" else TOL64, ncol=1, radii=[4.0])
+
+
+def test_lc_off_and_flow_off_switches(P):
+    L = (20, 16, 12)
+    for lc, flow in ((False, True), (True, False)):
+        p = dict(synth.NEMATIC)
+        g = P.Solver(*L, precision=P.LC_FP64, lc=lc, flow=flow, body_force=(1e-5, 0, 0), **p)
+        o = oracle.Oracle(*L, lc=lc, flow=flow, body_force=(1e-5, 0, 0), **p)
+        for s in (g, o):
+            s.init_uniaxial((0, 1, 1), amp=1e-2, seed=4)
+            s.add_colloid((9.5, 7.5, 5.5), 3.5, 1, 0.01)
+        g.step(30)
+        o.step(30)
+        compare(g, o, TOL64, ncol=1, radii=[3.5])
+
+
+# ------------------------------------------------------------ invariants --
+def test_mass_and_momentum_fp32(P):
+    L = (32, 32, 32)
+    w = synth.workload("nematic32")
+    g = P.Solver(*L, precision=P.LC_FP32, **w["params"])
+    g.init_uniaxial((0, 0, 1), amp=1e-2, seed=1)
+    g.add_colloid((15.5, 15.5, 15.5), 4.0, P.LC_PLANAR, 0.01)
+    d0 = g.diag()
+    g.step(200)
+    d1 = g.diag()
+    c = g.colloid(0)
+    assert abs(d1["mass"] - d0["mass"]) / d0["mass"] < 1e-7
+    # FP32 deviation storage: per-node rounding of the collision (~1e-10)
+    np.testing.assert_allclose(d1["momentum"] + c["impulse"], d0["momentum"], atol=1e-6)
+
+
+def test_poiseuille_magic_tau_fp64(P):
+    tau, gx, nz = 0.5 + math.sqrt(3 / 16), 1e-6, 16
+    g = P.Solver(4, 3, nz, wall_z=True, precision=P.LC_FP64, tau=tau, lc=False, body_force=(gx, 0, 0))
+    g.step(8000)
+    _, u = g.get_rho_u()
+    nu = (tau - 0.5) / 3
+    z = np.arange(nz)
+    ana = gx / (2 * nu) * (z + 0.5) * (nz - 0.5 - z)
+    np.testing.assert_allclose(u[0, :, 1, 2], ana, rtol=1e-9)
+
+
+def test_diagnostics_match_oracle(P):
+    L = (24, 20, 16)
+    p = dict(synth.NEMATIC, q0=2 * math.pi / 16)
+    cols = [dict(X=(11.2, 9.8, 7.7), a0=4.4, anchoring=0, w=0.02)]
+    g, o = make_pair(P, L, p, P.LC_FP64, colloids=cols, init=("helix", 2, 1e-2, 3))
+    g.step(20)
+    o.step(20)
+    dg, do = g.diag(), o.diag()
+    assert dg["n_fluid"] == do["n_fluid"]
+    assert dg["n_defect"] == do["n_defect"]
+    assert abs(dg["mass"] - do["mass"]) < 1e-9
+    np.testing.assert_allclose(dg["momentum"], do["momentum"], atol=1e-12)
+    assert abs(dg["free_energy"] - do["free_energy"]) < 1e-10 * abs(do["free_energy"]) + 1e-14
+    assert abs(dg["resid_rms"] - do["resid_rms"]) < 1e-9 * do["resid_rms"]
+    assert abs(dg["resid_max"] - do["resid_max"]) < 1e-9 * do["resid_max"]
+
+
+def test_helix_relaxes_to_discrete_closed_form_fp32(P):
+    """GPU relaxation (flow off) of the helix matches the (a, b) of the discrete
+    closed form within the FP32 tolerance."""
+    from test_oracle_lc import helix_equations, newton_ab
+    q0 = 2 * math.pi / 32
+    g = P.Solver(2, 2, 32, precision=P.LC_FP32, A0=1.0, gamma=3.0, K=0.065, q0=q0, Gamma=0.5, flow=False)
+    g.init_helix(2, 0.0, 0)
+    g.step(3000)
+    a, b = newton_ab(helix_equations(1.0, 3.0, 0.065, q0), 0.25, 0.5 / 6)
+    Q = g.get_Q()[:, :, 0, 0]
+    bz = (Q[0] + Q[3]) / 2
+    assert np.abs(bz - b).max() < 1e-5
+    assert np.abs(np.hypot(Q[0] - bz, Q[1]) - a).max() < 1e-5
+
+
+def test_relax_driver_reaches_tolerance(P):
+    g = P.Solver(8, 8, 8, precision=P.LC_FP64, **dict(synth.PAPER, K=0.065), flow=False)
+    g.init_uniaxial((0, 0, 1), amp=2e-2, seed=5)
+    steps, r = g.relax(tol=1e-10, max_steps=5000, check_every=100)
+    assert r <= 1e-10 and steps < 5000
+    Q = g.get_Q().reshape(5, -1)
+    for i in range(0, Q.shape[1], 37):
+        xx, xy, xz, yy, yz = Q[:, i]
+        lam = np.linalg.eigvalsh(np.array([[xx, xy, xz], [xy, yy, yz], [xz, yz, -xx - yy]]))[-1]
+        assert abs(1.5 * lam - 0.5) < 1e-8
+
+
+# -------------------------------------------------------------- batches --
+def test_batch_matches_single_boxes(P):
+    boxes = [dict(grid=(33, 21, 17), params=dict(synth.NEMATIC, q0=2 * math.pi / 17)),
+             dict(grid=(16, 16, 16), params=dict(synth.NEMATIC)),
+             dict(grid=(40, 12, 9), params=dict(synth.NEMATIC, A0=0.05))]
+    cols = [dict(X=(16.0, 10.0, 8.0), a0=4.5, anchoring=1, w=0.02), dict(X=(7.5, 7.5, 7.5), a0=3.0),
+            dict(X=(20.2, 5.5, 4.1), a0=3.3, anchoring=0, w=0.01)]
+    B = P.Batch(boxes, precision=P.LC_FP64)
+    singles = []
+    for i, (bx, c) in enumerate(zip(boxes, cols)):
+        B.boxes[i].init_uniaxial((0.1, 0.2, 1.0), amp=1e-2, seed=i)
+        B.boxes[i].add_colloid(c["X"], c["a0"], c.get("anchoring", 0), c.get("w", float("inf")))
+        s = P.Solver(*bx["grid"], precision=P.LC_FP64, **bx["params"])
+        s.init_uniaxial((0.1, 0.2, 1.0), amp=1e-2, seed=i)
+        s.add_colloid(c["X"], c["a0"], c.get("anchoring", 0), c.get("w", float("inf")))
+        singles.append(s)
+    B.step(25)
+    for s in singles:
+        s.step(25)
+    for i, s in enumerate(singles):
+        np.testing.assert_allclose(B.boxes[i].get_Q(), s.get_Q(), atol=1e-14)
+        np.testing.assert_allclose(B.boxes[i].get_f(), s.get_f(), atol=1e-14)
+    # and box 0 against the oracle
+    o = oracle.Oracle(*boxes[0]["grid"], threads=8, **boxes[0]["params"])
+    o.init_uniaxial((0.1, 0.2, 1.0), amp=1e-2, seed=0)
+    o.add_colloid(cols[0]["X"], cols[0]["a0"], 1, 0.02)
+    o.step(25)
+    compare(B.boxes[0], o, TOL64, ncol=1, radii=[cols[0]["a0"]])
+
+
+# ------------------------------------------------------- full-size sample --
+def test_chol128_full_size_fp32_steps(P):
+    """128^3 cholesteric with an R = 8 normal-anchored colloid in the launch
+    configuration the bench times: 3 steps against the oracle at full size."""
+    w = synth.workload("chol128_R8")
+    c = w["colloids"][0]
+    g, o = make_pair(P, w["grid"], w["params"], P.LC_FP32, colloids=[c],
+                     init=("helix", 2, w["init"]["amp"], w["init"]["seed"]), threads=16)
+    g.step(3)
+    o.step(3)
+    compare(g, o, TOL32, ncol=1, radii=[c["a0"]])
