@@ -68,8 +68,8 @@ __device__ __forceinline__ void warp_flush_colloid(DevColloid* col, int c, doubl
     const bool mine = (c == cc);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      const double t = warp_sum(mine ? v[k] : 0.0);
-      if (lane == leader && t != 0.0) atomicAdd(&col[cc].acc[off + k], t);
+      const double t = warp_sum(mine ? v[k] : 0.0);  // total lands in lane 0
+      if (lane == 0 && t != 0.0) atomicAdd(&col[cc].acc[off + k], t);
     }
     if (mine) c = -1;
     pend = __ballot_sync(0xffffffffu, c >= 0);
@@ -494,6 +494,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_links(const DevBox* __restrict__ boxes, const int2* __restrict__ chunks,
                                                int nchunks) {
   __shared__ DevBox B;
+  __shared__ double sblk[6];
+  __shared__ int sc0;
   const int tid = threadIdx.x;
   for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const int2 cd = chunks[ch];
@@ -503,6 +505,10 @@ __global__ void __launch_bounds__(256) k_links(const DevBox* __restrict__ boxes,
     const int l = cd.y + tid;
     int my_c = -1;
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    // the chunk's first colloid is summed in shared memory (links are sorted by colloid)
+    if (tid < 6) sblk[tid] = 0.0;
+    if (tid == 0) sc0 = (cd.y < nl && cd.y < B.nlinks_cap) ? (int)B.link_col[cd.y] : -1;
+    __syncthreads();
     if (l < nl && l < B.nlinks_cap) {
       const int i = B.link_node[l];
       const int q = B.link_dir[l];
@@ -534,7 +540,20 @@ __global__ void __launch_bounds__(256) k_links(const DevBox* __restrict__ boxes,
         v[3 + a] = tq[a];
       }
     }
-    warp_flush_colloid(B.col, my_c, v, 0);
+    const int c0 = sc0;
+    const bool main = (my_c == c0) && c0 >= 0;
+    const bool warp_main = __all_sync(0xffffffffu, main || my_c < 0);
+    if (warp_main) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const double t = warp_sum(v[k]);
+        if ((tid & 31) == 0 && t != 0.0) atomicAdd(&sblk[k], t);
+      }
+    } else {
+      warp_flush_colloid(B.col, my_c, v, 0);
+    }
+    __syncthreads();
+    if (tid < 6 && c0 >= 0 && sblk[tid] != 0.0) atomicAdd(&B.col[c0].acc[tid], sblk[tid]);
   }
 }
 
