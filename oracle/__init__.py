@@ -4,7 +4,7 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It wraps ``lclb_oracle.c`` (plain C,
 FP64, no code shared with the CUDA library) through ctypes.  The C source
 cites, function by function, the passage of Lintuvuori et al. (Sec. 2,
-Eqs. 1-7) it follows.
+Eqs. 1-8) it follows.
 """
 from __future__ import annotations
 

@@ -232,14 +232,14 @@ static void principal_dir(const double q[3][3], double n[3]) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Order-parameter boundary value at a solid node (Sec. 2.2, Eq. 6).   */
+/* Order-parameter boundary value at a solid node (Sec. 2.2, Eq. 7).   */
 /* ------------------------------------------------------------------ */
 /* Surface value seen by fluid node (its Q is qf) across the face to solid
  * node (sx,sy,sz) of colloid c, or to a wall when c < 0.
  *  - homeotropic: n0 = unit outward normal s at the solid node;
  *  - planar: n0 = projection of the fluid node's director (principal
  *    eigenvector of qf) on the tangent plane normal to s;
- *  - Q0 = S0 (n0 n0 - delta/3) (Eq. 6);
+ *  - Q0 = S0 (n0 n0 - delta/3) (Eq. 7);
  *  - strong anchoring (the paper's rule): the solid node takes Q0;
  *  - finite anchoring strength w: the value minimising the surface term
  *    (w/2)|Qs - Q0|^2 plus the face gradient term (K/2)|Qs - qf|^2, i.e.
@@ -445,7 +445,7 @@ static void lc_fields(oracle* o) {
 /* Body force on the fluid: discrete divergence of P over control-volume
  * faces (Sec. 2.2).  A fluid-fluid face carries (P_i + P_j)/2; a face to a
  * solid node or a wall carries P_i (extrapolation).  The colloid receives
- * the opposite of each of its faces' contributions (Eq. 7, summed over the
+ * the opposite of each of its faces' contributions (Eq. 8, summed over the
  * solid-fluid faces), and the torque of that force about its centre taken
  * at the face centre. */
 static void lc_force(oracle* o) {
@@ -909,7 +909,7 @@ static double init_noise(uint64_t seed, long i, int k, double amp) {
   return amp * (2.0 * u - 1.0);
 }
 
-/* Uniaxial Q = S0 (n n - delta/3) (the uniaxial form below Eq. 6 of Sec. 2.1)
+/* Uniaxial Q = S0 (n n - delta/3) (the uniaxial form stated with Eq. 6, Sec. 2.1)
  * plus seeded noise on the 5 stored components; f at rest equilibrium. */
 void oracle_init_uniaxial(oracle* o, const double* n, double amp, uint64_t seed) {
   long N = o->N;

@@ -214,7 +214,7 @@ __device__ void principal_dir(const T* q, T n[3]) {
   n[0] = c[0] * s; n[1] = c[1] * s; n[2] = c[2] * s;
 }
 
-// Surface order Q0 = S0 (n0 n0 - delta/3) (Eq. 6) at solid node (sx,sy,sz) of
+// Surface order Q0 = S0 (n0 n0 - delta/3) (Eq. 7) at solid node (sx,sy,sz) of
 // colloid c (c < 0: a z wall, homeotropic along z).  Homeotropic: n0 = unit
 // normal s at the solid node; planar: n0 = projection of the fluid node's
 // director (principal eigenvector of qf) on the plane normal to s.

@@ -1,6 +1,6 @@
 // lclb_kernels.cu -- sm_103a kernels of one coupled step (Lintuvuori et al., Sec. 2.2):
 //   k_force   LC stress at fluid nodes, its face divergence (body force) and the
-//             colloid LC force/torque (Eqs. 4, 7); z-marching tiles with the
+//             colloid LC force/torque (Eqs. 4, 8); z-marching tiles with the
 //             stress of three planes in shared memory.
 //   k_lb      pull-scheme stream + BGK collide with Guo forcing, bounce-back on
 //             links inline (moving-surface term), writes df* and u.
