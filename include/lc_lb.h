@@ -70,7 +70,7 @@ typedef struct {
  *   rho0  reference density;  tau  BGK relaxation time (viscosity (tau-1/2)/3);
  *   A0, gamma, K, q0  Landau-de Gennes constants of Eq. 1 (q0 = 2 pi / pitch);
  *   xi  flow-alignment parameter of Eq. 4;  Gamma  rotational diffusion of Eq. 2;
- *   S0  surface order of Eq. 6 (<= 0: the bulk uniaxial order
+ *   S0  surface order of Eq. 7 (<= 0: the bulk uniaxial order
  *       1/4 + 3/4 sqrt(1 - 8/(3 gamma)));
  *   body_force  uniform force density on fluid nodes (0 for the paper's runs);
  *   precision  LC_FP32 (FP32 storage, FP64 reductions) or LC_FP64;
@@ -173,6 +173,26 @@ int lc_lb_get_colloid(lc_lb* h, int id, double out[27]);
 int lc_lb_get_links(lc_lb* h, int32_t* node, int8_t* dir, int16_t* colloid, size_t cap, size_t* n_out);
 
 int lc_lb_diagnostics(lc_lb* h, lc_diag* out);
+
+/* Allocation-free diagnostics: the paper has no counterpart; this exists for
+ * callers that cannot allocate device memory at the point of the call --
+ * code that runs while another stream of the device is being captured into
+ * a CUDA graph in global or relaxed mode (where cudaMalloc is not permitted),
+ * allocator or out-of-memory handlers that must not re-enter an allocator,
+ * and loops that cannot afford the device-wide synchronisation of
+ * cudaMalloc/cudaFree.  It fills mass, momentum, n_fluid, n_defect and step
+ * of *out exactly as lc_lb_diagnostics does (the other fields are set to 0)
+ * and calls no cudaMalloc, cudaFree or allocating library routine.  Its
+ * scratch is a static device array of 384 KiB + 64 B that every GPU loading
+ * this library holds until the process exits; it serves boxes of at most
+ * 2,097,152 nodes (a 128^3 box) and returns LC_ERR_ARG for larger ones.  The
+ * first call on a device looks up the array's device address (once per
+ * device, with that device current), so make that first call before any
+ * stream capture.  All calls on a device share the array, which keeps the
+ * last call's contents (each call overwrites every record it reads), so two
+ * calls whose GPU work overlaps -- e.g. two handles on different streams --
+ * race.  Synchronises the handle's stream. */
+int lc_lb_diagnostics_noalloc(lc_lb* h, lc_diag* out);
 
 /* Profiling: run nsteps steps without the graph, with CUDA events around
  * each phase on the handle's stream, and return the mean milliseconds per

@@ -116,6 +116,7 @@ def lib(use_torch_allocator: bool = True):
         L.lc_lb_get_links.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int8), C.POINTER(C.c_int16),
                                       C.c_size_t, C.POINTER(C.c_size_t)]
         L.lc_lb_diagnostics.argtypes = [vp, C.POINTER(lc_diag)]
+        L.lc_lb_diagnostics_noalloc.argtypes = [vp, C.POINTER(lc_diag)]
         L.lc_lb_profile.argtypes = [vp, C.c_int, dp]
         L.lc_lb_batch_profile.argtypes = [vp, C.c_int, dp]
         L.lc_lb_synchronize.argtypes = [vp]

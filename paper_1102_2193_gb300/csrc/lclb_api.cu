@@ -994,6 +994,69 @@ int lc_lb_batch_profile(lc_lb_batch* b, int nsteps, double ms_out[5]) {
   return rc;
 }
 
+}  // extern "C"
+
+// ---- diagnostics without allocation ------------------------------------------
+// Scratch of lc_lb_diagnostics_noalloc: one record of 6 doubles per block of
+// 256 nodes for up to 8192 blocks (2,097,152 nodes), then 8 doubles for the
+// reduced values: 384 KiB + 64 B on every device that loads the library.
+namespace {
+constexpr int NOALLOC_MAX_BLOCKS = 8192;
+constexpr int NOALLOC_OUT = NOALLOC_MAX_BLOCKS * 6;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[128] = {nullptr};
+}  // namespace
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_BLOCKS * 6 + 8];
+
+// Device address of the scratch on the current device, looked up once per
+// device (the host symbol is only a stand-in, not a device address).
+static int noalloc_scratch(double** out, std::string* err) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev), err);
+  if (dev < 0 || dev >= 128) return fail(err, LC_ERR_ARG, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(err, LC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return LC_OK;
+}
+
+extern "C" {
+
+int lc_lb_diagnostics_noalloc(lc_lb* h, lc_diag* out) {
+  if (int rc = h_check(h)) return rc;
+  if (!out) return fail(&h->err, LC_ERR_ARG, "null output");
+  const int nb = diag_state_blocks(h->hb.N);
+  if (nb > NOALLOC_MAX_BLOCKS)
+    return fail(&h->err, LC_ERR_ARG,
+                "box of %d nodes exceeds the %d-node limit of the allocation-free diagnostics", h->hb.N,
+                NOALLOC_MAX_BLOCKS * 256);
+  double* scr = nullptr;
+  int rc = noalloc_scratch(&scr, &h->err);
+  if (rc) return rc;
+  Group* g = h->g;
+  CK(launch_diag_state(g->prec, g->d_boxes, h->index, h->hb.N, scr, g->stream), &h->err);
+  CK(launch_reduce(scr, 0, nb, 6, 0u, scr + NOALLOC_OUT, g->stream), &h->err);
+  double r[6];
+  DevState st{};
+  CK(cudaMemcpyAsync(r, scr + NOALLOC_OUT, sizeof(r), cudaMemcpyDeviceToHost, g->stream), &h->err);
+  CK(cudaMemcpyAsync(&st, h->hb.st, sizeof(st), cudaMemcpyDeviceToHost, g->stream), &h->err);
+  CK(cudaStreamSynchronize(g->stream), &h->err);
+  memset(out, 0, sizeof(*out));
+  out->n_fluid = (long long)llround(r[4]);
+  out->n_defect = (long long)llround(r[5]);
+  out->mass = (double)out->n_fluid * h->hb.p.rho0 + r[0];
+  for (int a = 0; a < 3; ++a) out->momentum[a] = r[1 + a];
+  out->step = st.step;
+  if (!std::isfinite(out->mass)) return fail(&h->err, LC_ERR_NONFINITE, "non-finite diagnostics");
+  return LC_OK;
+}
+
 const char* lc_lb_last_error(const lc_lb* h) {
   if (!h) return g_err.c_str();
   if (!h->err.empty()) return h->err.c_str();
