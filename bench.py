@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS of coupled LB+Beris–Edwards step; time-to-relaxed-defect vs plain"
-LB_BYTES = 19 * 4 * 2          # algorithmic bytes per fluid node of the LB kernel (df read + write, FP32)
+FLB_BYTES = 19 * 4 * 2 + 5 * 4 + 3 * 4  # fused stress/force/LB kernel per node: df read + write, Q read, u write (FP32)
 STEP_BYTES = (19 + 5) * 4 * 2  # algorithmic bytes per node of the whole coupled step (df and Q, read + write)
 KERNEL_SOURCES = ("paper_1102_2193_gb300/csrc/lclb_kernels.cu", "paper_1102_2193_gb300/csrc/lclb_dev.cuh")
 
@@ -246,9 +246,9 @@ def run_gpu(args, ws, rank, local):
     # ---- per-phase launch durations: events around each kernel on the launching stream ----
     prof = s.profile(max(10, min(200, args.steps // 5)))
     peaks = measured_peaks()
-    lb_ms = prof["lb"]
-    achieved = LB_BYTES * nfluid / (lb_ms / 1e3) / 1e9
-    traffic = ncu_traffic("k_lb", args.workload)
+    flb_ms = prof["flb"]
+    achieved = FLB_BYTES * N / (flb_ms / 1e3) / 1e9
+    traffic = ncu_traffic("k_flb", args.workload)
     step_ms = ms / args.steps
     step_gbs = STEP_BYTES * N / (step_ms / 1e3) / 1e9
 
@@ -289,14 +289,14 @@ def run_gpu(args, ws, rank, local):
                         pitch=round(2 * 3.141592653589793 / w["params"]["q0"], 6) if w["params"]["q0"] else None,
                         storage="FP32 (df deviation, Q) with FP64 reductions",
                         l2="inputs larger than L2 (state ~0.45 GB per box); no flush", parallelism=f"replicas x{ws}"),
-            roofline=dict(kernel="k_lb (pull collide-stream + bounce-back)", bound="hbm", achieved=achieved,
-                          peak=peaks["hbm"], unit="GB/s", frac=achieved / peaks["hbm"], traffic=traffic,
-                          bytes_per_node=LB_BYTES, units_per_launch=nfluid, launch_ms=lb_ms,
+            roofline=dict(kernel="k_flb (LC stress + body force + pull collide-stream, fused)", bound="hbm",
+                          achieved=achieved, peak=peaks["hbm"], unit="GB/s", frac=achieved / peaks["hbm"],
+                          traffic=traffic, bytes_per_node=FLB_BYTES, units_per_launch=N, launch_ms=flb_ms,
                           peak_source=f"{peaks['src']} hbm_gbs"),
             step_roofline=dict(bound="hbm", achieved=step_gbs, peak=peaks["hbm"], unit="GB/s",
                                frac=step_gbs / peaks["hbm"], bytes_per_node=STEP_BYTES,
                                note="whole coupled step: 192 B/node algorithmic (df + Q, read + write)"),
-            phase_ms=prof, cpu_baseline=cpu, e2e=e2e, gpu_launches=5 * args.steps, clocks=clocks)
+            phase_ms=prof, cpu_baseline=cpu, e2e=e2e, gpu_launches=4 * args.steps, clocks=clocks)
         print(json.dumps(out), flush=True)
     if dist:
         torch.distributed.destroy_process_group()

@@ -194,11 +194,11 @@ int lc_lb_diagnostics(lc_lb* h, lc_diag* out);
  * race.  Synchronises the handle's stream. */
 int lc_lb_diagnostics_noalloc(lc_lb* h, lc_diag* out);
 
-/* Profiling: run nsteps steps without the graph, with CUDA events around
- * each phase on the handle's stream, and return the mean milliseconds per
- * launch of: [0] LC stress + body force, [1] LB collide/stream, [2] Q
- * update, [3] link momentum exchange, [4] colloid update.  The state
- * advances by nsteps.  Synchronises. */
+/* Profiling: run nsteps steps without the graph and with every kernel on
+ * the handle's stream, with CUDA events around each, and return the mean
+ * milliseconds per launch of: [0] fused LC stress + body force + LB
+ * collide/stream, [1] Q update, [2] link momentum exchange, [3] colloid
+ * update, [4] the whole step.  The state advances by nsteps.  Synchronises. */
 int lc_lb_profile(lc_lb* h, int nsteps, double ms_out[5]);
 int lc_lb_batch_profile(lc_lb_batch* b, int nsteps, double ms_out[5]);
 int lc_lb_synchronize(lc_lb* h);

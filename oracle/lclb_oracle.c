@@ -732,7 +732,10 @@ static void collide_stream(oracle* o) {
  * that becomes fluid takes f = f_eq(rho_bar, u_b) with rho_bar the mean
  * density of its fluid face neighbours (rho0 if none) and u_b the rigid
  * velocity there, whose momentum the colloid gives up, and Q = the mean of
- * its fluid face neighbours (+x,-x,+y,-y,+z,-z order). */
+ * its fluid face neighbours (+x,-x,+y,-y,+z,-z order).  The momentum
+ * exchanged is summed per colloid (u_b taken with the velocity before the
+ * exchange) and then changes the colloid's velocity by dp/M, so that fluid
+ * momentum + M V is conserved. */
 static void rediscretise(oracle* o) {
   long N = o->N;
   int16_t* ns = (int16_t*)malloc(sizeof(int16_t) * (size_t)N);
@@ -741,6 +744,8 @@ static void rediscretise(oracle* o) {
   for (long i = 0; i < N; ++i)
     if (ns[i] != o->solid[i]) { changed = 1; break; }
   if (!changed) { free(ns); return; }
+  double dpc[OMAXC][3];
+  memset(dpc, 0, sizeof(dpc));
   for (int z = 0; z < o->nz; ++z)
     for (int y = 0; y < o->ny; ++y)
       for (int x = 0; x < o->nx; ++x) {
@@ -748,7 +753,10 @@ static void rediscretise(oracle* o) {
         if (o->solid[i] < 0 && ns[i] >= 0) { /* covered */
           int c = ns[i];
           for (int q = 0; q < NQ; ++q)
-            for (int a = 0; a < 3; ++a) o->col[c].imp[a] += o->f[q * N + i] * CV[q][a];
+            for (int a = 0; a < 3; ++a) {
+              o->col[c].imp[a] += o->f[q * N + i] * CV[q][a];
+              dpc[c][a] += o->f[q * N + i] * CV[q][a];
+            }
           for (int q = 0; q < NQ; ++q) o->f[q * N + i] = 0.0;
         }
       }
@@ -780,7 +788,10 @@ static void rediscretise(oracle* o) {
           rigid_u(o, c, x, y, z, ub);
           feq_full(rb, ub, feq);
           for (int q = 0; q < NQ; ++q) o->f[q * N + i] = feq[q];
-          for (int a = 0; a < 3; ++a) o->col[c].imp[a] -= rb * ub[a];
+          for (int a = 0; a < 3; ++a) {
+            o->col[c].imp[a] -= rb * ub[a];
+            dpc[c][a] -= rb * ub[a];
+          }
           if (cnt) {
             for (int a = 0; a < 3; ++a)
               for (int b = 0; b < 3; ++b) qsum[a][b] /= cnt;
@@ -790,6 +801,9 @@ static void rediscretise(oracle* o) {
       }
   memcpy(o->solid, ns, sizeof(int16_t) * (size_t)N);
   free(ns);
+  for (int c = 0; c < o->ncol; ++c)
+    if (o->col[c].mobile)
+      for (int a = 0; a < 3; ++a) o->col[c].V[a] += dpc[c][a] / o->col[c].M;
 }
 
 /* Colloid update, explicit ("molecular dynamics-like", Sec. 2.2):

@@ -19,7 +19,7 @@ LC_OK, LC_ERR_ARG, LC_ERR_CUDA, LC_ERR_OOM, LC_ERR_OVERLAP, LC_ERR_NONFINITE, LC
 LC_FP32, LC_FP64 = 0, 1
 LC_NORMAL, LC_PLANAR = 0, 1
 LC_Q, LC_U, LC_RHO, LC_F_PRE, LC_FORCE, LC_SOLID = 0, 1, 2, 3, 4, 5
-PHASES = ("force", "lb", "lc", "links", "colloid")
+PHASES = ("flb", "lc", "links", "colloid", "step")
 _NCOMP = {LC_Q: 5, LC_U: 3, LC_RHO: 1, LC_F_PRE: 19, LC_FORCE: 3, LC_SOLID: 1}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))

@@ -101,9 +101,13 @@ struct Group {
   Mem mem;
   std::vector<lc_lb*> boxes;
   DevBox* d_boxes = nullptr;
-  Phase ph[3];  // force, lb, lc
+  Phase ph[4];  // 0 force (diagnostics/export), 1 lb (unused by the step), 2 lc, 3 fused force+lb (step)
+  cudaStream_t side = nullptr;   // second stream: link momentum exchange runs beside the Q update
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int2* d_chunks = nullptr;
   int nchunks = 0, chunk_cap = 0;
+  int2* d_mob = nullptr;        // (box, colloid) of every mobile colloid
+  int nmob = 0, mob_cap = 0;
   double* d_scratch = nullptr;  // FP64 export buffer
   size_t scratch_cap = 0;
   double* d_red = nullptr;      // reduction outputs
@@ -169,7 +173,7 @@ int build_phase(Group* g, int k) {
   P.d_tiles = (int4*)galloc(g, sizeof(int4) * tl.size());
   if (!P.d_tiles) return fail(&g->err, LC_ERR_OOM, "tile list allocation failed");
   CK(cudaMemcpyAsync(P.d_tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice, g->stream), &g->err);
-  const int width = k == 0 ? 1 : (k == 1 ? 4 : 2);
+  const int width = k == 0 ? 1 : (k == 1 ? 4 : (k == 2 ? 2 : 1));
   const size_t need = (size_t)width * tl.size();
   if (need > P.part_cap) {
     if (P.d_part) g->mem.put(P.d_part, g->al);
@@ -338,6 +342,13 @@ Group* new_group(int prec, void* stream, int nboxes, std::string* err) {
     }
     g->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    fail(err, LC_ERR_CUDA, "cannot create the side stream");
+    delete g;
+    return nullptr;
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -361,6 +372,12 @@ void free_group(Group* g) {
   if (g->graph) cudaGraphDestroy(g->graph);
   g->mem.release(g->al);
   if (g->h_red) cudaFreeHost(g->h_red);
+  if (g->side) {
+    cudaStreamSynchronize(g->side);
+    cudaStreamDestroy(g->side);
+  }
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_join) cudaEventDestroy(g->ev_join);
   if (g->own_stream) cudaStreamDestroy(g->stream);
   for (lc_lb* h : g->boxes) delete h;
   delete g;
@@ -389,11 +406,10 @@ void tune_file_load() {
   FILE* f = fopen(path, "r");
   if (!f) return;
   long long sig;
-  int prec, v[9];
-  while (fscanf(f, "%lld %d %d %d %d %d %d %d %d %d %d", &sig, &prec, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
-                &v[7], &v[8]) == 11) {
-    std::vector<TileCfg> c(3);
-    for (int k = 0; k < 3; ++k) c[k] = TileCfg{v[3 * k], v[3 * k + 1], v[3 * k + 2]};
+  int prec, v[6];
+  while (fscanf(f, "%lld %d %d %d %d %d %d %d", &sig, &prec, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 8) {
+    std::vector<TileCfg> c(2);
+    for (int k = 0; k < 2; ++k) c[k] = TileCfg{v[3 * k], v[3 * k + 1], v[3 * k + 2]};
     g_tune_cache[TuneKey(sig, prec)] = c;
   }
   fclose(f);
@@ -405,40 +421,42 @@ void tune_file_store(const TuneKey& key, const std::vector<TileCfg>& c) {
   FILE* f = fopen(path, "a");
   if (!f) return;
   fprintf(f, "%lld %d", std::get<0>(key), std::get<1>(key));
-  for (int k = 0; k < 3; ++k) fprintf(f, " %d %d %d", c[k].ty, c[k].zc, c[k].persistent);
+  for (int k = 0; k < 2; ++k) fprintf(f, " %d %d %d", c[k].ty, c[k].zc, c[k].persistent);
   fprintf(f, "\n");
   fclose(f);
 }
 
 cudaError_t launch_phase(Group* g, int k, int mode, int box = -1) {
   Launch L = phase_launch(g, k, box);
-  double* part = g->ph[k].d_part + (box < 0 ? 0 : (size_t)g->ph[k].start[box] * (k == 0 ? 1 : (k == 1 ? 4 : 2)));
+  const int width = k == 0 ? 1 : (k == 1 ? 4 : (k == 2 ? 2 : 1));
+  double* part = g->ph[k].d_part + (box < 0 ? 0 : (size_t)g->ph[k].start[box] * width);
   if (k == 0) return launch_force(g->prec, L, mode, part);
   if (k == 1) return launch_lb(g->prec, L, mode, part);
-  return launch_lc(g->prec, L, mode, part);
+  if (k == 2) return launch_lc(g->prec, L, mode, part);
+  return launch_flb(g->prec, L, mode, part);
 }
 
 // Time every candidate tile shape of each phase on the group's own state (the
 // phase kernels are idempotent between parity flips) and keep the fastest.
 int autotune_group(Group* g, std::string* desc) {
-  const int tys[3] = {2, 4, 8};
   const int zcs[7] = {1, 2, 4, 8, 16, 32, 64};
-  const int pers[3] = {0, 4, 8};
+  const int pers[3] = {0, 2, 4};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), &g->err);
   CK(cudaEventCreate(&e1), &g->err);
   char buf[256];
   std::string out;
-  for (int k = 0; k < 3; ++k) {
+  for (int k : {3, 2}) {
     TileCfg best = g->ph[k].cfg;
     float best_ms = 1e30f;
+    const std::vector<int> tys = k == 3 ? std::vector<int>{4, 6, 8} : std::vector<int>{2, 4, 8};
     for (int ty : tys)
       for (int zc : zcs)
         for (int pp : pers) {
-          if (k == 0 && g->prec == LC_FP64 && ty == 8) continue;
+          if (k == 3 && zc < 2) continue;
           g->ph[k].cfg = TileCfg{ty, zc, pp};
           if (build_phase(g, k)) return LC_ERR_OOM;
-          const int mode = k == 2 ? LC_RESID : 0;
+          const int mode = k == 2 ? LC_RESID : 0;  // no colloid accumulation while tuning
           CK(launch_phase(g, k, mode), &g->err);  // warm-up
           CK(cudaEventRecord(e0, g->stream), &g->err);
           for (int r = 0; r < 3; ++r) CK(launch_phase(g, k, mode), &g->err);
@@ -453,15 +471,15 @@ int autotune_group(Group* g, std::string* desc) {
         }
     g->ph[k].cfg = best;
     if (build_phase(g, k)) return LC_ERR_OOM;
-    snprintf(buf, sizeof(buf), "%s:ty=%d,zc=%d,pers=%d(%.1fus) ", k == 0 ? "force" : (k == 1 ? "lb" : "lc"), best.ty,
-             best.zc, best.persistent, 1000.f * best_ms / 3.f);
+    snprintf(buf, sizeof(buf), "%s:ty=%d,zc=%d,pers=%d(%.1fus) ", k == 3 ? "flb" : "lc", best.ty, best.zc,
+             best.persistent, 1000.f * best_ms / 3.f);
     out += buf;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_tune_cache[tune_key(g)] = {g->ph[0].cfg, g->ph[1].cfg, g->ph[2].cfg};
+    g_tune_cache[tune_key(g)] = {g->ph[3].cfg, g->ph[2].cfg};
     tune_file_store(tune_key(g), g_tune_cache[tune_key(g)]);
   }
   g->tuned = true;
@@ -480,12 +498,13 @@ int maybe_tune(Group* g) {
     }
     auto it = g_tune_cache.find(tune_key(g));
     if (it != g_tune_cache.end()) {
-      for (int k = 0; k < 3; ++k) g->ph[k].cfg = it->second[k];
+      g->ph[3].cfg = it->second[0];
+      g->ph[2].cfg = it->second[1];
       g->tuned = true;
     }
   }
   if (g->tuned) {
-    for (int k = 0; k < 3; ++k)
+    for (int k : {2, 3})
       if (build_phase(g, k)) return LC_ERR_OOM;
     return LC_OK;
   }
@@ -498,12 +517,57 @@ int maybe_tune(Group* g) {
 }
 
 // ---- one step -----------------------------------------------------------------
+// One coupled step: fused stress + body force + collide/stream, then the Q
+// update on the main stream and the link momentum exchange on the side
+// stream (both read only what the fused kernel wrote), joined before the
+// colloid update.
 int enqueue_step(Group* g) {
-  CK(launch_phase(g, 0, FORCE_ACC), &g->err);
-  CK(launch_phase(g, 1, 0), &g->err);
+  CK(launch_phase(g, 3, FORCE_ACC), &g->err);
+  if (g->nchunks > 0) {
+    CK(cudaEventRecord(g->ev_fork, g->stream), &g->err);
+    CK(cudaStreamWaitEvent(g->side, g->ev_fork, 0), &g->err);
+    CK(launch_links(g->prec, g->d_boxes, g->d_chunks, g->nchunks, g->nchunks, g->side), &g->err);
+    CK(cudaEventRecord(g->ev_join, g->side), &g->err);
+  }
   CK(launch_phase(g, 2, LC_RESID), &g->err);
-  CK(launch_links(g->prec, g->d_boxes, g->d_chunks, g->nchunks, g->nchunks, g->stream), &g->err);
+  if (g->nchunks > 0) CK(cudaStreamWaitEvent(g->stream, g->ev_join, 0), &g->err);
   CK(launch_colloid(g->d_boxes, (int)g->boxes.size(), g->stream), &g->err);
+  if (g->nmob > 0)
+    CK(launch_rediscretise(g->prec, g->d_boxes, (int)g->boxes.size(), g->d_mob, g->nmob, g->nsm, g->stream), &g->err);
+  return LC_OK;
+}
+
+// Mobile colloid list of the group and change-list capacity of each box.
+int build_mobile(Group* g) {
+  std::vector<int2> mob;
+  for (size_t b = 0; b < g->boxes.size(); ++b) {
+    lc_lb* h = g->boxes[b];
+    int need = 0;
+    for (size_t c = 0; c < h->col.size(); ++c)
+      if (h->col[c].mobile) {
+        mob.push_back(make_int2((int)b, (int)c));
+        const int e = (int)std::ceil(2.0 * h->col[c].a0) + 5;
+        need += e * e * e;
+      }
+    if (need > h->hb.chg_cap) {
+      if (h->hb.chg) g->mem.put(h->hb.chg, g->al);
+      h->hb.chg = (int*)galloc(g, sizeof(int) * 2 * (size_t)need);
+      if (!h->hb.chg) return fail(&h->err, LC_ERR_OOM, "change-list allocation failed");
+      h->hb.chg_cap = need;
+      int rc = upload_box(g, h);
+      if (rc) return rc;
+    }
+  }
+  if ((int)mob.size() > g->mob_cap) {
+    if (g->d_mob) g->mem.put(g->d_mob, g->al);
+    g->mob_cap = (int)mob.size() + 8;
+    g->d_mob = (int2*)galloc(g, sizeof(int2) * g->mob_cap);
+    if (!g->d_mob) return fail(&g->err, LC_ERR_OOM, "mobile list allocation failed");
+  }
+  g->nmob = (int)mob.size();
+  if (!mob.empty())
+    CK(cudaMemcpyAsync(g->d_mob, mob.data(), sizeof(int2) * mob.size(), cudaMemcpyHostToDevice, g->stream), &g->err);
+  g->dirty = true;
   return LC_OK;
 }
 
@@ -541,22 +605,26 @@ int group_profile(Group* g, int n, double* ms) {
   double acc[5] = {0, 0, 0, 0, 0};
   for (int s = 0; s < n; ++s) {
     CK(cudaEventRecord(ev[0], g->stream), &g->err);
-    CK(launch_phase(g, 0, FORCE_ACC), &g->err);
+    CK(launch_phase(g, 3, FORCE_ACC), &g->err);
     CK(cudaEventRecord(ev[1], g->stream), &g->err);
-    CK(launch_phase(g, 1, 0), &g->err);
-    CK(cudaEventRecord(ev[2], g->stream), &g->err);
     CK(launch_phase(g, 2, LC_RESID), &g->err);
-    CK(cudaEventRecord(ev[3], g->stream), &g->err);
+    CK(cudaEventRecord(ev[2], g->stream), &g->err);
     CK(launch_links(g->prec, g->d_boxes, g->d_chunks, g->nchunks, g->nchunks, g->stream), &g->err);
-    CK(cudaEventRecord(ev[4], g->stream), &g->err);
+    CK(cudaEventRecord(ev[3], g->stream), &g->err);
     CK(launch_colloid(g->d_boxes, (int)g->boxes.size(), g->stream), &g->err);
-    CK(cudaEventRecord(ev[5], g->stream), &g->err);
-    CK(cudaEventSynchronize(ev[5]), &g->err);
-    for (int k = 0; k < 5; ++k) {
+    if (g->nmob > 0)
+      CK(launch_rediscretise(g->prec, g->d_boxes, (int)g->boxes.size(), g->d_mob, g->nmob, g->nsm, g->stream),
+         &g->err);
+    CK(cudaEventRecord(ev[4], g->stream), &g->err);
+    CK(cudaEventSynchronize(ev[4]), &g->err);
+    for (int k = 0; k < 4; ++k) {
       float t = 0.f;
       cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
       acc[k] += t;
     }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[0], ev[4]);
+    acc[4] += t;
   }
   for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
   for (int k = 0; k < 5; ++k) ms[k] = n > 0 ? acc[k] / n : 0.0;
@@ -690,7 +758,7 @@ int lc_lb_create(const lc_grid* grid, const lc_params* params, void* stream, lc_
   g->boxes.push_back(h);
   rc = make_box(g, grid, params, h);
   if (!rc) rc = rebuild_geometry(h);
-  for (int k = 0; k < 3 && !rc; ++k) rc = build_phase(g, k);
+  for (int k = 0; k < 4 && !rc; ++k) rc = build_phase(g, k);
   if (!rc) rc = build_chunks(g);
   if (rc) {
     g_err = h->err.empty() ? g->err : h->err;
@@ -799,6 +867,7 @@ int lc_lb_add_colloid(lc_lb* h, const double X[3], double a0, int anchoring, dou
     if (rc) return rc;
     return fail(&h->err, LC_ERR_OVERLAP, "colloid overlaps another colloid");
   }
+  if (C.mobile && (rc = build_mobile(g))) return rc;
   if (id_out) *id_out = id;
   return LC_OK;
 }
@@ -934,13 +1003,26 @@ int lc_lb_get_links(lc_lb* h, int32_t* node, int8_t* dir, int16_t* colloid, size
   if (n_out) *n_out = (size_t)n;
   const size_t k = std::min(cap, (size_t)n);
   if (k == 0) return LC_OK;
-  std::vector<int8_t> c8(k);
-  if (node) CK(cudaMemcpyAsync(node, h->hb.link_node, sizeof(int) * k, cudaMemcpyDeviceToHost, g->stream), &h->err);
-  if (dir) CK(cudaMemcpyAsync(dir, h->hb.link_dir, k, cudaMemcpyDeviceToHost, g->stream), &h->err);
-  CK(cudaMemcpyAsync(c8.data(), h->hb.link_col, k, cudaMemcpyDeviceToHost, g->stream), &h->err);
+  // the device list is in node order after a full build and unordered after a
+  // re-discretisation: return it sorted by (colloid, node, direction)
+  std::vector<int> nd((size_t)n);
+  std::vector<int8_t> dr((size_t)n), c8((size_t)n);
+  CK(cudaMemcpyAsync(nd.data(), h->hb.link_node, sizeof(int) * n, cudaMemcpyDeviceToHost, g->stream), &h->err);
+  CK(cudaMemcpyAsync(dr.data(), h->hb.link_dir, n, cudaMemcpyDeviceToHost, g->stream), &h->err);
+  CK(cudaMemcpyAsync(c8.data(), h->hb.link_col, n, cudaMemcpyDeviceToHost, g->stream), &h->err);
   CK(cudaStreamSynchronize(g->stream), &h->err);
-  if (colloid)
-    for (size_t i = 0; i < k; ++i) colloid[i] = c8[i];
+  std::vector<size_t> ord((size_t)n);
+  for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) {
+    if (c8[a] != c8[b]) return c8[a] < c8[b];
+    if (nd[a] != nd[b]) return nd[a] < nd[b];
+    return dr[a] < dr[b];
+  });
+  for (size_t i = 0; i < k; ++i) {
+    if (node) node[i] = nd[ord[i]];
+    if (dir) dir[i] = dr[ord[i]];
+    if (colloid) colloid[i] = c8[ord[i]];
+  }
   return LC_OK;
 }
 
@@ -1085,7 +1167,7 @@ int lc_lb_batch_create(int n, const lc_grid* grids, const lc_params* params, voi
     if (!rc) rc = rebuild_geometry(h);
     if (rc) g_err = h->err;
   }
-  for (int k = 0; k < 3 && !rc; ++k) rc = build_phase(g, k);
+  for (int k = 0; k < 4 && !rc; ++k) rc = build_phase(g, k);
   if (!rc) rc = build_chunks(g);
   if (rc) {
     free_group(g);

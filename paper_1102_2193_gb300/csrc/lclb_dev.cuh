@@ -59,6 +59,7 @@ struct DevColloid {
   double acc[12];
   double Fh[3], Th[3], Flc[3], Tlc[3];
   double imp[3], aimp[3];
+  double rdp[3];  // momentum exchanged by the running re-discretisation
 };
 
 // Per-box state flags kept on the device (the step kernels flip the buffer
@@ -67,14 +68,17 @@ struct DevState {
   int fpar;       // f[fpar] holds the current populations
   int qpar;       // Q[qpar] holds the current order parameter
   int pre_valid;  // f[fpar] holds pre-collision values: next collide reads them in place
-  int err;        // sticky error bits (1: link list overflow, 2: re-discretisation overflow)
+  int err;        // sticky error bits (1: link list overflow, 2: change list overflow, 4: overlap)
+  int nchg;       // nodes whose solid/fluid status changes after the colloid update of this step
+  int pad;
   long long step;
 };
 
 struct DevBox {
   int nx, ny, nz, wall_z;
   int N, ncol;
-  int nlinks_cap, pad;
+  int nlinks_cap, chg_cap;
+  int* chg;             // change list: (node, colloid << 1 | uncovered) pairs
   void* f[2];
   void* Q[2];
   void* u;
@@ -469,6 +473,115 @@ __device__ __forceinline__ void stress(const PhysT<T>& P, const T q[5], const T 
            T(2) * xi / T(3) * qab(h, a, b) + A[a][b] - A[b][a];
       p[3 * a + b] = v;
     }
+}
+
+// All liquid-crystal quantities of one fluid node from its Q and its face-
+// neighbour values, sharing intermediates: Q.Q (for H and Tr Q^3), the curl
+// C_ab = eps_agd d_g Q_db (for the chiral part of H and of f'), and
+// <d_a Q, d_b Q> for the 6 symmetric pairs (its trace is |grad Q|^2).
+//   H   = cb Q + A0 g (Q.Q - Tr(Q^2) I/3) + K lap Q - 2 K q0 (C + C^T),
+//         cb = -A0(1 - g/3) - A0 g Tr(Q^2) - 4 K q0^2                       (Eqs. 1, 2)
+//   f'  = A0/2 (1-g/3) Tr Q^2 - A0 g/3 Tr Q^3 + A0 g/4 (Tr Q^2)^2
+//         + K/2 |grad Q|^2 + 2 K q0 Q:C + 2 K q0^2 Tr Q^2                    (Eq. 1)
+//   P   = f' I + 2 xi (Q + I/3) Q:H - xi (A + A^T) - (2 xi/3) H - E + A - A^T,
+//         A = Q H,  E_ab = K <d_a Q, d_b Q> + 2 K q0 sum_gn d_a Q_gn eps_mbg Q_mn  (Eq. 4)
+// The same expressions as molecular_field / free_energy_density / stress.
+template <typename T, bool NEED_P>
+__device__ __forceinline__ void lc_node(const PhysT<T>& P, const T qi[5], const T qn[6][5], T h[5], T p[9],
+                                        T* fprime) {
+  T dq[3][5], lap[5];
+  derivatives(qi, qn, dq, lap);
+  const T A0 = P.A0, g = P.gamma, K = P.K, q0 = P.q0;
+  T Q[3][3], D[3][3][3], S2[3][3], C[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      Q[a][b] = qab(qi, a, b);
+#pragma unroll
+      for (int gg = 0; gg < 3; ++gg) D[gg][a][b] = qab(dq[gg], a, b);
+    }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a; b < 3; ++b) {
+      S2[a][b] = Q[a][0] * Q[0][b] + Q[a][1] * Q[1][b] + Q[a][2] * Q[2][b];
+      S2[b][a] = S2[a][b];
+    }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) C[a][b] = D[(a + 1) % 3][(a + 2) % 3][b] - D[(a + 2) % 3][(a + 1) % 3][b];
+  const T trq2 = S2[0][0] + S2[1][1] + S2[2][2];
+  const T cb = -A0 * (T(1) - g / T(3)) - A0 * g * trq2 - T(4) * K * q0 * q0;
+  const T A0g = A0 * g, twoKq0 = T(2) * K * q0;
+  T H[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a; b < 3; ++b) {
+      const int k = a == 0 ? b : (a == 1 ? 2 + b : 5);
+      const T lp = k < 5 ? lap[k] : -lap[0] - lap[3];
+      T v = cb * Q[a][b] + A0g * (S2[a][b] - (a == b ? trq2 / T(3) : T(0))) + K * lp - twoKq0 * (C[a][b] + C[b][a]);
+      H[a][b] = v;
+      H[b][a] = v;
+    }
+  h[0] = H[0][0]; h[1] = H[0][1]; h[2] = H[0][2]; h[3] = H[1][1]; h[4] = H[1][2];
+  if (!NEED_P) return;
+  T E[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a; b < 3; ++b) {
+      T e = T(0);
+#pragma unroll
+      for (int gg = 0; gg < 3; ++gg)
+#pragma unroll
+        for (int n = 0; n < 3; ++n) e += D[a][gg][n] * D[b][gg][n];
+      E[a][b] = K * e;
+      E[b][a] = K * e;
+    }
+  const T Kgrad2 = E[0][0] + E[1][1] + E[2][2];  // K |grad Q|^2
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T e2 = T(0);
+#pragma unroll
+      for (int gg = 0; gg < 3; ++gg) {
+        if (gg == b) continue;
+        const int m = 3 - b - gg;
+        const T sgn = ((m - b + 3) % 3 == 2) ? T(1) : T(-1);  // eps(m, b, gg)
+        e2 += sgn * (D[a][gg][0] * Q[m][0] + D[a][gg][1] * Q[m][1] + D[a][gg][2] * Q[m][2]);
+      }
+      E[a][b] += twoKq0 * e2;
+    }
+  T trq3 = T(0), qc = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      trq3 += Q[a][b] * S2[a][b];
+      qc += Q[a][b] * C[a][b];
+    }
+  const T fp = T(0.5) * A0 * (T(1) - g / T(3)) * trq2 - A0g / T(3) * trq3 + T(0.25) * A0g * trq2 * trq2 +
+               T(0.5) * Kgrad2 + twoKq0 * qc + T(2) * K * q0 * q0 * trq2;
+  T Am[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) Am[a][b] = Q[a][0] * H[0][b] + Q[a][1] * H[1][b] + Q[a][2] * H[2][b];
+  const T qh = Am[0][0] + Am[1][1] + Am[2][2];
+  const T xi = P.xi;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const T dlt = a == b ? T(1) : T(0);
+      p[3 * a + b] = fp * dlt + T(2) * xi * (Q[a][b] + dlt / T(3)) * qh - xi * (Am[a][b] + Am[b][a]) -
+                     T(2) * xi / T(3) * H[a][b] - E[a][b] + Am[a][b] - Am[b][a];
+    }
+  *fprime = fp;
 }
 
 }  // namespace lclb

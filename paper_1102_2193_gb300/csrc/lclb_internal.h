@@ -29,9 +29,13 @@ struct Launch {
 
 cudaError_t launch_force(int prec, const Launch& L, int mode, double* part);
 cudaError_t launch_lb(int prec, const Launch& L, int mode, double* part);
+cudaError_t launch_flb(int prec, const Launch& L, int mode, double* part);  // ty in {4, 6, 8}
 cudaError_t launch_lc(int prec, const Launch& L, int mode, double* part);
 cudaError_t launch_links(int prec, const DevBox* boxes, const int2* chunks, int nchunks, int grid, cudaStream_t s);
 cudaError_t launch_colloid(DevBox* boxes, int nboxes, cudaStream_t s);
+// Re-discretisation after the colloid update; mob lists (box, colloid) of mobile colloids.
+cudaError_t launch_rediscretise(int prec, DevBox* boxes, int nboxes, const int2* mob, int nmob, int nsm,
+                                cudaStream_t s);
 cudaError_t launch_geometry(DevBox* boxes, int b, int N, cudaStream_t s);
 cudaError_t launch_link_build(DevBox* boxes, int b, int N, int c, int* blocksum, int base, int* total,
                               cudaStream_t s);

@@ -83,7 +83,79 @@ __device__ __forceinline__ void load_box(DevBox& sb, const DevBox* boxes, int b)
 }
 
 // ---------------------------------------------------------------------------
-// k_force
+// shared pieces of the force / LB kernels
+// ---------------------------------------------------------------------------
+// Stress P (9 comps) of fluid node (gx,gy,kk) into sP[c*HP] (c = 0..8); the
+// node's mask byte decides fluid/solid.  Returns the flag stored with it:
+// 0 fluid, colloid id + 1, or WALLFLAG.
+template <typename T>
+__device__ __forceinline__ uint8_t stress_at(const DevBox& B, const PhysT<T>& PP, const T* __restrict__ Q, int gx,
+                                             int gy, int kk, T* sP, int HP, bool fe, double* fe_acc) {
+  const int i = gx + B.nx * (gy + B.ny * kk);
+  const uint8_t m = B.mask[i];
+  const uint8_t flag = m & IDMASK;
+  if (flag != 0) return flag;
+  T qi[5], qn[6][5], h[5], p[9], fp;
+  double surf = 0.0;
+  gather_q(B, Q, gx, gy, kk, i, m, qi, qn, fe ? &surf : nullptr);
+  lc_node<T, true>(PP, qi, qn, h, p, &fp);
+#pragma unroll
+  for (int c = 0; c < 9; ++c) sP[c * HP] = p[c];
+  if (fe) *fe_acc += (double)fp + surf;
+  return 0;
+}
+
+// Body force at interior fluid position pc (plane slot s0; the planes below
+// and above in slots sm, sp): F_a = sum_d [P_ad(face +d) - P_ad(face -d)],
+// a fluid-fluid face carrying (P_i + P_j)/2 and a solid or wall face P_i.
+// Each colloid face adds -(+-P_.d(i)) to the colloid's LC force (and its
+// moment about X to the torque) in the thread's accumulator.
+template <typename T>
+__device__ __forceinline__ void face_force(const DevBox& B, const T* sP, const uint8_t* sFl, int HP, int HX, int s0,
+                                           int sm, int sp, int pc, int x, int y, int kc, bool acc, T Fv[3],
+                                           int& my_c, double my_acc[6]) {
+  Fv[0] = Fv[1] = Fv[2] = T(0);
+  const int nslot[6] = {s0, s0, s0, s0, sp, sm};
+  const int npos[6] = {pc + 1, pc - 1, pc + HX, pc - HX, pc, pc};
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const int ax = d >> 1;
+    const T sgn = (d & 1) ? T(-1) : T(1);
+    const uint8_t fj = sFl[nslot[d] * HP + npos[d]];
+    T pcv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      pcv[a] = sP[(s0 * 9 + 3 * a + ax) * HP + pc];
+      const T face = (fj == 0) ? T(0.5) * (pcv[a] + sP[(nslot[d] * 9 + 3 * a + ax) * HP + npos[d]]) : pcv[a];
+      Fv[a] += sgn * face;
+    }
+    if (acc && fj != 0 && fj != WALLFLAG) {
+      const int c = fj - 1;
+      const DevColloid& C = B.col[c];
+      const double ff[3] = {-(double)sgn * (double)pcv[0], -(double)sgn * (double)pcv[1], -(double)sgn * (double)pcv[2]};
+      double r[3];
+      const double hx2 = 0.5 * (double)(ax == 0 ? sgn : 0), hy2 = 0.5 * (double)(ax == 1 ? sgn : 0),
+                   hz2 = 0.5 * (double)(ax == 2 ? sgn : 0);
+      disp(B, (double)x + hx2, (double)y + hy2, (double)kc + hz2, C.X, r);
+      const double tq[3] = {r[1] * ff[2] - r[2] * ff[1], r[2] * ff[0] - r[0] * ff[2], r[0] * ff[1] - r[1] * ff[0]};
+      if (my_c >= 0 && my_c != c) {  // a second colloid at this node: flush the first directly
+        for (int a = 0; a < 6; ++a) {
+          atomicAdd(&B.col[my_c].acc[6 + a], my_acc[a]);
+          my_acc[a] = 0.0;
+        }
+      }
+      my_c = c;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        my_acc[a] += ff[a];
+        my_acc[3 + a] += tq[a];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_force: body force (and, in diagnostic mode, free-energy partials) alone
 // ---------------------------------------------------------------------------
 // Shared memory: P of three z planes over the tile plus a one-node halo,
 // [3][9][(TX+2)(TY+2)] in T, then one flag byte per position.
@@ -103,7 +175,7 @@ __global__ void __launch_bounds__(TX * TY) k_force(const DevBox* __restrict__ bo
     load_box(B, boxes, td.x);
     if (!B.p.lc_on) continue;
     const PhysT<T>& PP = phys<T>(B);
-    int my_c = -1;  // colloid whose LC force this thread is accumulating
+    int my_c = -1;
     double my_acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     const T* __restrict__ Q = static_cast<const T*>(B.Q[B.st->qpar]);
     T* __restrict__ Fout = static_cast<T*>(B.F);
@@ -113,7 +185,6 @@ __global__ void __launch_bounds__(TX * TY) k_force(const DevBox* __restrict__ bo
     const int zend = min(z0 + zc, nz);
     double fe_acc = 0.0;
     __syncthreads();
-
     for (int k = z0 - 1; k <= zend; ++k) {
       const int slot = (k - z0 + 1) % 3;
       const bool wallplane = B.wall_z && (k < 0 || k >= nz);
@@ -123,79 +194,24 @@ __global__ void __launch_bounds__(TX * TY) k_force(const DevBox* __restrict__ bo
         if (hx > vx + 1 || hy > vy + 1) continue;
         uint8_t flag = WALLFLAG;
         if (!wallplane) {
-          const int gx = wrapn(x0 - 1 + hx, nx), gy = wrapn(y0 - 1 + hy, ny);
-          const int i = gx + nx * (gy + ny * kk);
-          const uint8_t m = B.mask[i];
-          flag = m & IDMASK;
-          if (flag == 0) {
-            const bool interior = (mode & FORCE_FE) && hx >= 1 && hx <= vx && hy >= 1 && hy <= vy && k >= z0 &&
-                                  k < zend;
-            T qi[5], qn[6][5], dq[3][5], lap[5], h[5], p[9];
-            double surf = 0.0;
-            gather_q(B, Q, gx, gy, kk, i, m, qi, qn, interior ? &surf : nullptr);
-            derivatives(qi, qn, dq, lap);
-            molecular_field(PP, qi, dq, lap, h);
-            const T fp = free_energy_density(PP, qi, dq);
-            stress(PP, qi, dq, h, fp, p);
-#pragma unroll
-            for (int c = 0; c < 9; ++c) sP[(slot * 9 + c) * HP + pidx] = p[c];
-            if (interior) fe_acc += (double)fp + surf;
-          }
+          const bool interior = (mode & FORCE_FE) && hx >= 1 && hx <= vx && hy >= 1 && hy <= vy && k >= z0 && k < zend;
+          flag = stress_at(B, PP, Q, wrapn(x0 - 1 + hx, nx), wrapn(y0 - 1 + hy, ny), kk, sP + slot * 9 * HP + pidx,
+                           HP, interior, &fe_acc);
         }
         sFl[slot * HP + pidx] = flag;
       }
       __syncthreads();
       if (k >= z0 + 1) {
         const int kc = k - 1;
-        const int sm = (k - z0 - 1) % 3, s0 = (k - z0) % 3, sp = slot;
         const int tx = threadIdx.x, ty = threadIdx.y;
-        if (tx < vx && ty < vy) {
-          const int pc = (tx + 1) + HX * (ty + 1);
-          if (sFl[s0 * HP + pc] == 0) {
-            const int x = x0 + tx, y = y0 + ty;
-            T Fv[3] = {T(0), T(0), T(0)};
-            const int nslot[6] = {s0, s0, s0, s0, sp, sm};
-            const int npos[6] = {pc + 1, pc - 1, pc + HX, pc - HX, pc, pc};
+        const int pc = (tx + 1) + HX * (ty + 1);
+        if (tx < vx && ty < vy && sFl[((k - z0) % 3) * HP + pc] == 0) {
+          T Fv[3];
+          face_force(B, sP, sFl, HP, HX, (k - z0) % 3, (k - z0 - 1) % 3, slot, pc, x0 + tx, y0 + ty, kc,
+                     (mode & FORCE_ACC) != 0, Fv, my_c, my_acc);
+          const int ic = (x0 + tx) + nx * ((y0 + ty) + ny * kc);
 #pragma unroll
-            for (int d = 0; d < 6; ++d) {
-              const int ax = d >> 1;
-              const T sgn = (d & 1) ? T(-1) : T(1);
-              const uint8_t fj = sFl[nslot[d] * HP + npos[d]];
-              T pcv[3];
-#pragma unroll
-              for (int a = 0; a < 3; ++a) {
-                pcv[a] = sP[(s0 * 9 + 3 * a + ax) * HP + pc];
-                const T face = (fj == 0) ? T(0.5) * (pcv[a] + sP[(nslot[d] * 9 + 3 * a + ax) * HP + npos[d]]) : pcv[a];
-                Fv[a] += sgn * face;
-              }
-              if ((mode & FORCE_ACC) && fj != 0 && fj != WALLFLAG) {
-                const int c = fj - 1;
-                const DevColloid& C = B.col[c];
-                double ff[3] = {-(double)sgn * (double)pcv[0], -(double)sgn * (double)pcv[1],
-                                -(double)sgn * (double)pcv[2]};
-                double r[3];
-                const double hx2 = 0.5 * (double)(ax == 0 ? sgn : 0), hy2 = 0.5 * (double)(ax == 1 ? sgn : 0),
-                             hz2 = 0.5 * (double)(ax == 2 ? sgn : 0);
-                disp(B, (double)x + hx2, (double)y + hy2, (double)kc + hz2, C.X, r);
-                double tq[3] = {r[1] * ff[2] - r[2] * ff[1], r[2] * ff[0] - r[0] * ff[2], r[0] * ff[1] - r[1] * ff[0]};
-                if (my_c >= 0 && my_c != c) {  // a second colloid at this node: flush the first directly
-                  for (int a = 0; a < 6; ++a) {
-                    atomicAdd(&B.col[my_c].acc[6 + a], my_acc[a]);
-                    my_acc[a] = 0.0;
-                  }
-                }
-                my_c = c;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                  my_acc[a] += ff[a];
-                  my_acc[3 + a] += tq[a];
-                }
-              }
-            }
-            const int ic = x + nx * (y + ny * kc);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) Fout[(size_t)a * N + ic] = Fv[a];
-          }
+          for (int a = 0; a < 3; ++a) Fout[(size_t)a * N + ic] = Fv[a];
         }
       }
       __syncthreads();
@@ -210,7 +226,7 @@ __global__ void __launch_bounds__(TX * TY) k_force(const DevBox* __restrict__ bo
 }
 
 // ---------------------------------------------------------------------------
-// pull with bounce-back (shared by k_lb and the export/diagnostic kernels)
+// pull with bounce-back (shared by the LB kernels and the export/diagnostic kernels)
 // ---------------------------------------------------------------------------
 // Gathers the pre-collision deviations df_q(r) = df*_q(r - c_q) for fluid
 // node r, or, when r - c_q is solid (colloid) or beyond a wall, the bounced
@@ -269,19 +285,64 @@ __device__ __forceinline__ void pull(const DevBox& B, const T* __restrict__ fin,
   }
 }
 
+// Collide at fluid node i with force (Fx,Fy,Fz) (BGK + Guo, deviation form):
+// rho = rho0 + sum df, u = (sum df c + F/2)/rho,
+// df*_q = df_q - omega (df_q - df_eq_q) + (1 - 1/2tau) w_q [3(c - u) + 9 (c.u) c].F,
+// df_eq_q = w_q [drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u^2)].  Writes df* and u.
+template <typename T>
+__device__ __forceinline__ void collide_store(const PhysT<T>& PP, T* __restrict__ fout, T* __restrict__ ub, int N,
+                                              int i, const T df[NQ], T Fx, T Fy, T Fz) {
+  T drho = T(0), mx = T(0), my = T(0), mz = T(0);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    drho += df[q];
+    if (cx(q)) mx += cx(q) > 0 ? df[q] : -df[q];
+    if (cy(q)) my += cy(q) > 0 ? df[q] : -df[q];
+    if (cz(q)) mz += cz(q) > 0 ? df[q] : -df[q];
+  }
+  const T rho = PP.rho0 + drho;
+  const T inv = T(1) / rho;
+  const T ux = (mx + T(0.5) * Fx) * inv, uy = (my + T(0.5) * Fy) * inv, uz = (mz + T(0.5) * Fz) * inv;
+  const T usq = ux * ux + uy * uy + uz * uz;
+  const T uF = ux * Fx + uy * Fy + uz * Fz;
+  const T omega = PP.omega, pref = PP.pref;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const T w = T(wq(q));
+    const T cu = T(cx(q)) * ux + T(cy(q)) * uy + T(cz(q)) * uz;
+    const T cF = T(cx(q)) * Fx + T(cy(q)) * Fy + T(cz(q)) * Fz;
+    const T eq = w * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
+    const T src = pref * w * (T(3) * (cF - uF) + T(9) * cu * cF);
+    fout[(size_t)q * N + i] = df[q] - omega * (df[q] - eq) + src;
+  }
+  ub[i] = ux;
+  ub[(size_t)N + i] = uy;
+  ub[(size_t)2 * N + i] = uz;
+}
+
+template <typename T>
+__device__ __forceinline__ void solid_velocity(const DevBox& B, T* __restrict__ ub, int x, int y, int z, int i,
+                                               uint8_t m) {
+  const DevColloid& C = B.col[(m & IDMASK) - 1];
+  T ur[3];
+  rigid_velocity_t<T>(B, T(x), T(y), T(z), C.X, C.V, C.W, ur);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) ub[(size_t)a * B.N + i] = ur[a];
+}
+
 // ---------------------------------------------------------------------------
-// k_lb
+// k_lb: collide/stream with the body force read from memory
 // ---------------------------------------------------------------------------
 template <typename T, int TY>
-__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * TY)) k_lb(const DevBox* __restrict__ boxes, const int4* __restrict__ tiles,
-                                                int ntiles, int zc, int mode, double* __restrict__ part) {
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * TY)) k_lb(
+    const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
+    double* __restrict__ part) {
   __shared__ DevBox B;
-  __shared__ double sred[32 * 4];
-  const int tid = threadIdx.x + TX * threadIdx.y;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
     load_box(B, boxes, td.x);
     if (!B.p.flow_on) continue;
+    const PhysT<T>& PP = phys<T>(B);
     const int fpar = B.st->fpar;
     const bool pre = B.st->pre_valid != 0;
     const T* __restrict__ fin = static_cast<const T*>(B.f[fpar]);
@@ -291,70 +352,114 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * 
     const int nx = B.nx, ny = B.ny, N = B.N;
     const int x = td.y + threadIdx.x, y = td.z + threadIdx.y;
     const int zend = min(td.w + zc, B.nz);
-    const bool valid = x < nx && y < ny;
-    const PhysT<T>& PP = phys<T>(B);
-    const T rho0 = PP.rho0, omega = PP.omega, pref = PP.pref;
-    const T gx = PP.g[0], gy = PP.g[1], gz = PP.g[2];
+    if (x >= nx || y >= ny) continue;
     const bool lc = B.p.lc_on != 0;
-    double dsum[4] = {0.0, 0.0, 0.0, 0.0};
-    if (valid) {
-      for (int z = td.w; z < zend; ++z) {
-        const int i = x + nx * (y + ny * z);
+    for (int z = td.w; z < zend; ++z) {
+      const int i = x + nx * (y + ny * z);
+      const uint8_t m = B.mask[i];
+      if (m & IDMASK) {
+        solid_velocity(B, ub, x, y, z, i, m);
+        continue;
+      }
+      T df[NQ];
+      pull(B, fin, x, y, z, i, m, pre, df);
+      T Fx = PP.g[0], Fy = PP.g[1], Fz = PP.g[2];
+      if (lc) {
+        Fx += Fb[i];
+        Fy += Fb[(size_t)N + i];
+        Fz += Fb[(size_t)2 * N + i];
+      }
+      collide_store(PP, fout, ub, N, i, df, Fx, Fy, Fz);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_flb: stress + body force + collide/stream fused (the step kernel)
+// ---------------------------------------------------------------------------
+// Tile: 32 x BY interior columns marching z.  Threads: 32*(BY+2) cover the
+// stress positions of the tile rows and the two y-halo rows (whole warps),
+// one more warp the two x-halo columns, so every halo position of a plane is
+// computed in a single pass.  Warps 1..BY then run the body force and the LB
+// collide of their interior node; the stress never leaves shared memory and
+// the body force never reaches HBM.
+template <typename T, int BY>
+__global__ void __launch_bounds__(32 * (BY + 3), (sizeof(T) == 4 && BY <= 4) ? 2 : 1) k_flb(
+    const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
+    double* __restrict__ part) {
+  constexpr int HX = TX + 2, HY = BY + 2, HP = HX * HY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sP = reinterpret_cast<T*>(smem_raw);
+  uint8_t* sFl = smem_raw + sizeof(T) * 27 * HP;
+  __shared__ DevBox B;
+  const int tid = threadIdx.x;
+  // this thread's stress position (hx, hy) in the halo'd plane, or none
+  int hx, hy;
+  if (tid < 32 * HY) {
+    hx = 1 + (tid & 31);
+    hy = tid >> 5;
+  } else {
+    const int k = tid - 32 * HY;
+    hx = k < HY ? 0 : (k < 2 * HY ? HX - 1 : -1);
+    hy = k < HY ? k : k - HY;
+  }
+  const int pidx = hx >= 0 ? hx + HX * hy : -1;
+  const bool lbthread = tid >= 32 && tid < 32 * (BY + 1);
+  const int tx = tid & 31, ty = (tid >> 5) - 1;
+
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int4 td = tiles[t];
+    load_box(B, boxes, td.x);
+    const PhysT<T>& PP = phys<T>(B);
+    const bool lc = B.p.lc_on != 0, flow = B.p.flow_on != 0;
+    if (!flow && !lc) continue;
+    int my_c = -1;
+    double my_acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const T* __restrict__ Q = static_cast<const T*>(B.Q[B.st->qpar]);
+    const int fpar = B.st->fpar;
+    const bool pre = B.st->pre_valid != 0;
+    const T* __restrict__ fin = static_cast<const T*>(B.f[fpar]);
+    T* __restrict__ fout = static_cast<T*>(B.f[fpar ^ 1]);
+    T* __restrict__ ub = static_cast<T*>(B.u);
+    const int x0 = td.y, y0 = td.z, z0 = td.w;
+    const int nx = B.nx, ny = B.ny, nz = B.nz, N = B.N;
+    const int vx = min(TX, nx - x0), vy = min(BY, ny - y0);
+    const int zend = min(z0 + zc, nz);
+    const bool mypos = pidx >= 0 && hx <= vx + 1 && hy <= vy + 1;
+    const int gx = wrapn(x0 - 1 + hx, nx), gy = wrapn(y0 - 1 + hy, ny);
+    const bool myint = lbthread && tx < vx && ty < vy;
+    for (int k = z0 - 1; k <= zend; ++k) {
+      const int slot = (k - z0 + 1) % 3;
+      if (lc && mypos) {
+        const bool wallplane = B.wall_z && (k < 0 || k >= nz);
+        const int kk = B.wall_z ? k : wrapn(k, nz);
+        double dummy = 0.0;
+        sFl[slot * HP + pidx] =
+            wallplane ? WALLFLAG : stress_at(B, PP, Q, gx, gy, kk, sP + slot * 9 * HP + pidx, HP, false, &dummy);
+      }
+      __syncthreads();
+      if (k >= z0 + 1 && myint) {
+        const int kc = k - 1;
+        const int x = x0 + tx, y = y0 + ty;
+        const int i = x + nx * (y + ny * kc);
         const uint8_t m = B.mask[i];
         if (m & IDMASK) {
-          const DevColloid& C = B.col[(m & IDMASK) - 1];
-          T ur[3];
-          rigid_velocity_t<T>(B, T(x), T(y), T(z), C.X, C.V, C.W, ur);
-#pragma unroll
-          for (int a = 0; a < 3; ++a) ub[(size_t)a * N + i] = ur[a];
-          continue;
-        }
-        T df[NQ];
-        pull(B, fin, x, y, z, i, m, pre, df);
-        T drho = T(0), mx = T(0), my = T(0), mz = T(0);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          drho += df[q];
-          if (cx(q)) mx += cx(q) > 0 ? df[q] : -df[q];
-          if (cy(q)) my += cy(q) > 0 ? df[q] : -df[q];
-          if (cz(q)) mz += cz(q) > 0 ? df[q] : -df[q];
-        }
-        T Fx = gx, Fy = gy, Fz = gz;
-        if (lc) {
-          Fx += Fb[i];
-          Fy += Fb[(size_t)N + i];
-          Fz += Fb[(size_t)2 * N + i];
-        }
-        const T rho = rho0 + drho;
-        const T inv = T(1) / rho;
-        const T ux = (mx + T(0.5) * Fx) * inv, uy = (my + T(0.5) * Fy) * inv, uz = (mz + T(0.5) * Fz) * inv;
-        const T usq = ux * ux + uy * uy + uz * uz;
-        const T uF = ux * Fx + uy * Fy + uz * Fz;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          const T w = T(wq(q));
-          const T cu = T(cx(q)) * ux + T(cy(q)) * uy + T(cz(q)) * uz;
-          const T cF = T(cx(q)) * Fx + T(cy(q)) * Fy + T(cz(q)) * Fz;
-          const T eq = w * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
-          const T src = pref * w * (T(3) * (cF - uF) + T(9) * cu * cF);
-          fout[(size_t)q * N + i] = df[q] - omega * (df[q] - eq) + src;
-        }
-        ub[i] = ux;
-        ub[(size_t)N + i] = uy;
-        ub[(size_t)2 * N + i] = uz;
-        if (mode & LB_MOM) {
-          dsum[0] += (double)drho;
-          dsum[1] += (double)mx;
-          dsum[2] += (double)my;
-          dsum[3] += (double)mz;
+          if (flow) solid_velocity(B, ub, x, y, kc, i, m);
+        } else {
+          T Fv[3] = {T(0), T(0), T(0)};
+          if (lc)
+            face_force(B, sP, sFl, HP, HX, (k - z0) % 3, (k - z0 - 1) % 3, slot, (tx + 1) + HX * (ty + 1), x, y, kc,
+                       (mode & FORCE_ACC) != 0, Fv, my_c, my_acc);
+          if (flow) {
+            T df[NQ];
+            pull(B, fin, x, y, kc, i, m, pre, df);
+            collide_store(PP, fout, ub, N, i, df, Fv[0] + PP.g[0], Fv[1] + PP.g[1], Fv[2] + PP.g[2]);
+          }
         }
       }
+      __syncthreads();
     }
-    if (mode & LB_MOM) {
-      block_sum<4>(dsum, sred);
-      if (tid == 0)
-        for (int k = 0; k < 4; ++k) part[4 * t + k] = dsum[k];
-    }
+    if (mode & FORCE_ACC) warp_flush_colloid(B.col, my_c, my_acc, 6);
   }
 }
 
@@ -387,10 +492,9 @@ __global__ void __launch_bounds__(TX * TY) k_lc(const DevBox* __restrict__ boxes
         const int i = x + nx * (y + ny * z);
         const uint8_t m = B.mask[i];
         if (m & IDMASK) continue;
-        T qi[5], qn[6][5], dq[3][5], lap[5], h[5];
+        T qi[5], qn[6][5], h[5];
         gather_q(B, Q, x, y, z, i, m, qi, qn, nullptr);
-        derivatives(qi, qn, dq, lap);
-        molecular_field(PP, qi, dq, lap, h);
+        lc_node<T, false>(PP, qi, qn, h, nullptr, nullptr);
         int nb[6], zz[2];
         face_neighbours(B, x, y, z, nb, zz);
         T ui[3], un[6][3];
@@ -604,6 +708,7 @@ __global__ void k_colloid(DevBox* __restrict__ boxes, int nboxes) {
     }
     if (B.p.lc_on) st->qpar ^= 1;
     st->step += 1;
+    st->nchg = 0;
   }
 }
 
@@ -931,6 +1036,281 @@ __global__ void __launch_bounds__(256) k_reduce(const double* __restrict__ part,
 }
 
 // ---------------------------------------------------------------------------
+// re-discretisation of moving colloids (Sec. 2.2, last paragraph)
+// ---------------------------------------------------------------------------
+// Run after the colloid update of every step for the (box, colloid) pairs of
+// mobile colloids; every kernel returns at once when nothing changed.
+//   k_rd_find     nodes of the colloid's bounding region whose solid test at
+//                 the new X differs from the mask -> change list
+//   k_rd_pull     pre-collision populations of the step just streamed, pulled
+//                 with the old mask and the old colloid state, into the other
+//                 buffer (the next collide reads them in place)
+//   k_rd_apply    covered nodes hand their momentum sum_q df_q c_q to the
+//                 colloid; uncovered nodes take f_eq(rho_bar, u_b) and the
+//                 mean Q of their fluid face neighbours (fluid before and after)
+//   k_rd_mask     mask bits of the changed nodes; k_rd_near the near flags of
+//                 the region; k_rd_links the boundary links of the box.
+__device__ __forceinline__ int region_lo(double c, double r) { return (int)floor(c - r - 2.0); }
+
+// Node (x,y,z) of the bounding region of colloid C: index k of n = nx*ny*nz region
+// nodes; returns false when the region node falls outside a z wall.
+__device__ __forceinline__ bool region_node(const DevBox& B, const DevColloid& C, int k, int& x, int& y, int& z) {
+  const int lx = region_lo(C.X[0], C.a0), ly = region_lo(C.X[1], C.a0), lz = region_lo(C.X[2], C.a0);
+  const int ex = min(B.nx, (int)ceil(2.0 * C.a0) + 5), ey = min(B.ny, (int)ceil(2.0 * C.a0) + 5),
+            ez = min(B.nz, (int)ceil(2.0 * C.a0) + 5);
+  const int ix = k % ex, iy = (k / ex) % ey, iz = k / (ex * ey);
+  x = wrapn(lx + ix, B.nx);
+  y = wrapn(ly + iy, B.ny);
+  z = lz + iz;
+  if (B.wall_z) return z >= 0 && z < B.nz;
+  z = wrapn(z, B.nz);
+  return true;
+}
+
+__device__ __forceinline__ int region_size(const DevBox& B, const DevColloid& C) {
+  const int e = (int)ceil(2.0 * C.a0) + 5;
+  return min(B.nx, e) * min(B.ny, e) * min(B.nz, e);
+}
+
+// New solid owner of node (x,y,z): colloid index + 1, or 0.
+__device__ __forceinline__ int new_owner(const DevBox& B, int x, int y, int z) {
+  for (int c = 0; c < B.ncol; ++c)
+    if (inside_colloid(B, x, y, z, B.col[c])) return c + 1;
+  return 0;
+}
+
+__global__ void __launch_bounds__(256) k_rd_find(DevBox* __restrict__ boxes, const int2* __restrict__ mob, int nmob) {
+  for (int p = blockIdx.y; p < nmob; p += gridDim.y) {
+    const DevBox& B = boxes[mob[p].x];
+    const DevColloid& C = B.col[mob[p].y];
+    const int n = region_size(B, C);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+      int x, y, z;
+      if (!region_node(B, C, k, x, y, z)) continue;
+      const int i = x + B.nx * (y + B.ny * z);
+      const int old = B.mask[i] & IDMASK;
+      const bool in_new = inside_colloid(B, x, y, z, C);
+      const int c = mob[p].y;
+      int code = -1;
+      if (in_new && old == 0) code = c << 1;                 // covered
+      else if (!in_new && old == c + 1) code = (c << 1) | 1;  // uncovered
+      else if (in_new && old != 0 && old != c + 1) atomicOr(&B.st->err, 4);
+      if (code >= 0) {
+        const int slot = atomicAdd(&B.st->nchg, 1);
+        if (slot < B.chg_cap) {
+          B.chg[2 * slot] = i;
+          B.chg[2 * slot + 1] = code;
+        } else {
+          atomicOr(&B.st->err, 2);
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rd_pull(DevBox* __restrict__ boxes, int nboxes) {
+  for (int b = 0; b < nboxes; ++b) {
+    const DevBox& B = boxes[b];
+    if (B.st->nchg == 0 || !B.p.flow_on) continue;
+    const int fpar = B.st->fpar;
+    const bool pre = B.st->pre_valid != 0;
+    const T* fin = static_cast<const T*>(B.f[fpar]);
+    T* fpre = static_cast<T*>(B.f[fpar ^ 1]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.N; i += gridDim.x * blockDim.x) {
+      const uint8_t m = B.mask[i];
+      if (m & IDMASK) continue;
+      const int x = i % B.nx, y = (i / B.nx) % B.ny, z = i / (B.nx * B.ny);
+      T df[NQ];
+      pull(B, fin, x, y, z, i, m, pre, df);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) fpre[(size_t)q * B.N + i] = df[q];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rd_apply(DevBox* __restrict__ boxes, int nboxes) {
+  for (int b = 0; b < nboxes; ++b) {
+    DevBox& B = boxes[b];
+    const int nchg = min(B.st->nchg, B.chg_cap);
+    if (nchg == 0) continue;
+    const int fpar = B.st->fpar;
+    T* fpre = static_cast<T*>(B.f[fpar ^ 1]);
+    T* Q = static_cast<T*>(B.Q[B.st->qpar]);
+    const int N = B.N;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nchg; k += gridDim.x * blockDim.x) {
+      const int i = B.chg[2 * k], code = B.chg[2 * k + 1];
+      const int c = code >> 1;
+      DevColloid& C = B.col[c];
+      const int x = i % B.nx, y = (i / B.nx) % B.ny, z = i / (B.nx * B.ny);
+      if ((code & 1) == 0) {  // covered: its fluid momentum goes to the colloid
+        if (B.p.flow_on) {
+          double mom[3] = {0.0, 0.0, 0.0};
+          for (int q = 0; q < NQ; ++q) {
+            const double d = (double)fpre[(size_t)q * N + i];
+            mom[0] += cx(q) * d;
+            mom[1] += cy(q) * d;
+            mom[2] += cz(q) * d;
+            fpre[(size_t)q * N + i] = T(0);
+          }
+          for (int a = 0; a < 3; ++a) {
+            atomicAdd(&C.imp[a], mom[a]);
+            atomicAdd(&C.rdp[a], mom[a]);
+          }
+        }
+        continue;
+      }
+      // uncovered: neighbours fluid before and after
+      double rsum = 0.0, qsum[5] = {0, 0, 0, 0, 0};
+      int cnt = 0;
+      for (int d = 0; d < 6; ++d) {
+        int xx = x, yy = y, zz = z;
+        if (d == 0) xx = wrap1(x + 1, B.nx);
+        if (d == 1) xx = wrap1(x - 1, B.nx);
+        if (d == 2) yy = wrap1(y + 1, B.ny);
+        if (d == 3) yy = wrap1(y - 1, B.ny);
+        if (d == 4) zz = z + 1;
+        if (d == 5) zz = z - 1;
+        if (B.wall_z) {
+          if (zz < 0 || zz >= B.nz) continue;
+        } else {
+          zz = wrap1(zz, B.nz);
+        }
+        const int j = xx + B.nx * (yy + B.ny * zz);
+        if ((B.mask[j] & IDMASK) != 0 || new_owner(B, xx, yy, zz) != 0) continue;
+        double rj = B.p.rho0;
+        if (B.p.flow_on)
+          for (int q = 0; q < NQ; ++q) rj += (double)fpre[(size_t)q * N + j];
+        rsum += rj;
+        for (int kk = 0; kk < 5; ++kk) qsum[kk] += (double)Q[(size_t)kk * N + j];
+        ++cnt;
+      }
+      const double rb = cnt ? rsum / cnt : B.p.rho0;
+      double dd[3], ubv[3];
+      disp(B, (double)x, (double)y, (double)z, C.X, dd);
+      rigid_velocity(C.V, C.W, dd, ubv);
+      if (B.p.flow_on) {
+        const double uu = ubv[0] * ubv[0] + ubv[1] * ubv[1] + ubv[2] * ubv[2];
+        for (int q = 0; q < NQ; ++q) {
+          const double cu = cx(q) * ubv[0] + cy(q) * ubv[1] + cz(q) * ubv[2];
+          const double feq = wq(q) * rb * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+          fpre[(size_t)q * N + i] = T(feq - wq(q) * B.p.rho0);
+        }
+        for (int a = 0; a < 3; ++a) {
+          atomicAdd(&C.imp[a], -rb * ubv[a]);
+          atomicAdd(&C.rdp[a], -rb * ubv[a]);
+        }
+      }
+      if (cnt)
+        for (int kk = 0; kk < 5; ++kk) Q[(size_t)kk * N + i] = T(qsum[kk] / cnt);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_rd_mask(DevBox* __restrict__ boxes, int nboxes) {
+  for (int b = 0; b < nboxes; ++b) {
+    const DevBox& B = boxes[b];
+    const int nchg = min(B.st->nchg, B.chg_cap);
+    if (nchg == 0) continue;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nchg; k += gridDim.x * blockDim.x) {
+      const int i = B.chg[2 * k], code = B.chg[2 * k + 1];
+      B.mask[i] = (code & 1) ? (uint8_t)0 : (uint8_t)((code >> 1) + 1);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_rd_near(DevBox* __restrict__ boxes, const int2* __restrict__ mob, int nmob) {
+  for (int p = blockIdx.y; p < nmob; p += gridDim.y) {
+    const DevBox& B = boxes[mob[p].x];
+    if (B.st->nchg == 0) continue;
+    const DevColloid& C = B.col[mob[p].y];
+    const int n = region_size(B, C);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+      int x, y, z;
+      if (!region_node(B, C, k, x, y, z)) continue;
+      const int i = x + B.nx * (y + B.ny * z);
+      const uint8_t m = B.mask[i];
+      if (m & IDMASK) {
+        B.mask[i] = m & IDMASK;
+        continue;
+      }
+      bool near = false;
+      for (int q = 1; q < NQ; ++q) {
+        const int zz = z + cz(q);
+        if (B.wall_z && (zz < 0 || zz >= B.nz)) {
+          near = true;
+          continue;
+        }
+        const int j = wrap1(x + cx(q), B.nx) + B.nx * (wrap1(y + cy(q), B.ny) + B.ny * wrap1(zz, B.nz));
+        if (B.mask[j] & IDMASK) near = true;
+      }
+      B.mask[i] = near ? NEAR : (uint8_t)0;
+    }
+  }
+}
+
+// Rebuild the boundary links of boxes whose solid set changed (unordered;
+// lc_lb_get_links sorts them).  Block 0 of the grid first clears the count
+// in a separate launch (k_rd_links_reset).
+__global__ void k_rd_links_reset(DevBox* __restrict__ boxes, int nboxes) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nboxes && boxes[b].st->nchg > 0) *boxes[b].nlinks = 0;
+}
+
+__global__ void __launch_bounds__(256) k_rd_links(DevBox* __restrict__ boxes, int nboxes) {
+  for (int b = 0; b < nboxes; ++b) {
+    const DevBox& B = boxes[b];
+    if (B.st->nchg == 0) continue;
+    for (int c = blockIdx.y; c < B.ncol; c += gridDim.y) {
+      const DevColloid& C = B.col[c];
+      const int n = region_size(B, C);
+      for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int x, y, z;
+        if (!region_node(B, C, k, x, y, z)) continue;
+        const int i = x + B.nx * (y + B.ny * z);
+        unsigned bits;
+        const int nl = links_at(B, i, c, &bits);
+        if (!nl) continue;
+        int pos = atomicAdd(B.nlinks, nl);
+        for (int q = 1; q < NQ; ++q)
+          if (bits & (1u << q)) {
+            if (pos < B.nlinks_cap) {
+              B.link_node[pos] = i;
+              B.link_dir[pos] = (int8_t)q;
+              B.link_col[pos] = (int8_t)c;
+            } else {
+              atomicOr(&B.st->err, 1);
+            }
+            ++pos;
+          }
+      }
+    }
+  }
+}
+
+// The next collide reads the pulled populations in place; the momentum
+// exchanged by the re-discretisation changes each mobile colloid's velocity.
+__global__ void k_rd_finish(DevBox* __restrict__ boxes, int nboxes) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nboxes) return;
+  DevBox& B = boxes[b];
+  DevState* st = B.st;
+  if (st->nchg == 0) return;
+  if (B.p.flow_on) {
+    st->fpar ^= 1;
+    st->pre_valid = 1;
+  }
+  for (int c = 0; c < B.ncol; ++c) {
+    DevColloid& C = B.col[c];
+    if (C.mobile)
+      for (int a = 0; a < 3; ++a) C.V[a] += C.rdp[a] / C.M;
+    for (int a = 0; a < 3; ++a) C.rdp[a] = 0.0;
+  }
+  if (*B.nlinks > B.nlinks_cap) atomicOr(&st->err, 1);
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 template <typename T, int TY>
@@ -949,6 +1329,19 @@ static cudaError_t launch_force_t(const Launch& L, int mode, double* part) {
 template <typename T, int TY>
 static cudaError_t launch_lb_t(const Launch& L, int mode, double* part) {
   k_lb<T, TY><<<L.grid, dim3(TX, TY), 0, L.stream>>>(L.boxes, L.tiles, L.ntiles, L.zc, mode, part);
+  return cudaGetLastError();
+}
+
+template <typename T, int BY>
+static cudaError_t launch_flb_t(const Launch& L, int mode, double* part) {
+  constexpr int HP = (TX + 2) * (BY + 2);
+  const size_t smem = sizeof(T) * 27 * HP + 3 * HP;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_flb<T, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_flb<T, BY><<<L.grid, 32 * (BY + 3), smem, L.stream>>>(L.boxes, L.tiles, L.ntiles, L.zc, mode, part);
   return cudaGetLastError();
 }
 
@@ -973,6 +1366,22 @@ cudaError_t launch_force(int prec, const Launch& L, int mode, double* part) {
 cudaError_t launch_lb(int prec, const Launch& L, int mode, double* part) {
   if (prec == 0) { LCLB_DISPATCH_TY(launch_lb_t, float) }
   LCLB_DISPATCH_TY(launch_lb_t, double)
+}
+cudaError_t launch_flb(int prec, const Launch& L, int mode, double* part) {
+  if (prec == 0) {
+    switch (L.ty) {
+      case 4: return launch_flb_t<float, 4>(L, mode, part);
+      case 6: return launch_flb_t<float, 6>(L, mode, part);
+      case 8: return launch_flb_t<float, 8>(L, mode, part);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (L.ty) {
+    case 4: return launch_flb_t<double, 4>(L, mode, part);
+    case 6: return launch_flb_t<double, 6>(L, mode, part);
+    case 8: return launch_flb_t<double, 8>(L, mode, part);
+    default: return cudaErrorInvalidValue;
+  }
 }
 cudaError_t launch_lc(int prec, const Launch& L, int mode, double* part) {
   if (prec == 0) { LCLB_DISPATCH_TY(launch_lc_t, float) }
@@ -1024,6 +1433,23 @@ cudaError_t launch_set_field(int prec, DevBox* boxes, int b, int N, int which, c
 cudaError_t launch_export(int prec, const DevBox* boxes, int b, int N, int which, double* out, cudaStream_t s) {
   if (prec == 0) k_export<float><<<nblk(N, 256), 256, 0, s>>>(boxes, b, which, out);
   else k_export<double><<<nblk(N, 256), 256, 0, s>>>(boxes, b, which, out);
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_rediscretise(int prec, DevBox* boxes, int nboxes, const int2* mob, int nmob, int nsm,
+                                cudaStream_t s) {
+  if (nmob <= 0) return cudaSuccess;
+  k_rd_find<<<dim3(8, nmob), 256, 0, s>>>(boxes, mob, nmob);
+  if (prec == 0) k_rd_pull<float><<<nsm * 2, 256, 0, s>>>(boxes, nboxes);
+  else k_rd_pull<double><<<nsm * 2, 256, 0, s>>>(boxes, nboxes);
+  if (prec == 0) k_rd_apply<float><<<4, 256, 0, s>>>(boxes, nboxes);
+  else k_rd_apply<double><<<4, 256, 0, s>>>(boxes, nboxes);
+  k_rd_mask<<<4, 256, 0, s>>>(boxes, nboxes);
+  k_rd_near<<<dim3(8, nmob), 256, 0, s>>>(boxes, mob, nmob);
+  k_rd_links_reset<<<(nboxes + 127) / 128, 128, 0, s>>>(boxes, nboxes);
+  k_rd_links<<<dim3(8, 4), 256, 0, s>>>(boxes, nboxes);
+  k_rd_finish<<<(nboxes + 127) / 128, 128, 0, s>>>(boxes, nboxes);
   return cudaGetLastError();
 }
 

@@ -196,6 +196,26 @@ def test_walls_mobile_colloid(P, prec):
     compare(g, o, TOL32 if prec == "f32" else TOL64, ncol=1, radii=[4.0])
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_moving_colloid_rediscretisation(P, prec):
+    """A colloid launched across the lattice covers and uncovers nodes
+    (Sec. 2.2, last paragraph); the GPU re-discretises on the device."""
+    L = (24, 20, 18)
+    cols = [dict(X=(11.3, 9.6, 8.8), a0=3.6, anchoring=1, w=0.02, mobile=True)]
+    g, o = make_pair(P, L, dict(synth.NEMATIC), P.LC_FP32 if prec == "f32" else P.LC_FP64, colloids=cols,
+                     init=("uniaxial", (0, 0, 1), 1e-2, 3))
+    g.set_colloid_velocity(0, (0.02, -0.01, 0.015))
+    o.set_colloid_velocity(0, (0.02, -0.01, 0.015))
+    s0 = o.get_solid()
+    g.step(120)
+    o.step(120)
+    assert (o.get_solid() != s0).any()
+    compare(g, o, TOL32 if prec == "f32" else TOL64, ncol=1, radii=[3.6])
+    ng, dg, cg = g.links()
+    no, do, co = o.links()
+    assert (ng == no).all() and (dg == do).all() and (cg == co).all()
+
+
 def test_lc_off_and_flow_off_switches(P):
     L = (20, 16, 12)
     for lc, flow in ((False, True), (True, False)):

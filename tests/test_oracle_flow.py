@@ -175,3 +175,26 @@ def test_overlapping_colloids_rejected():
     o2 = oracle.Oracle(16, 16, 16, wall_z=True, lc=False)
     with pytest.raises(ValueError):
         o2.add_colloid((8.0, 8.0, 1.0), 3.0)
+
+
+def test_moving_colloid_rediscretisation_conserves_momentum():
+    """Sec. 2.2 (last paragraph): a colloid moving across the lattice covers and
+    uncovers nodes; the exchanged fluid momentum goes to the colloid, so fluid
+    momentum + M V is constant (no external force)."""
+    L = (24, 20, 18)
+    o = oracle.Oracle(*L, **dict(synth.NEMATIC), threads=4)
+    o.init_uniaxial((0, 0, 1), 1e-2, 3)
+    a0 = 3.6
+    cid = o.add_colloid((11.3, 9.6, 8.8), a0, oracle.PLANAR, 0.02, mobile=True)
+    o.set_colloid_velocity(cid, (0.02, -0.01, 0.015))
+    M = 4.0 / 3.0 * math.pi * a0**3
+    p0 = o.diag()["momentum"] + M * o.colloid(cid)["V"]
+    s0 = o.get_solid()
+    changes = 0
+    for _ in range(6):
+        o.step(20)
+        s = o.get_solid()
+        changes += int((s != s0).sum())
+        s0 = s
+        np.testing.assert_allclose(o.diag()["momentum"] + M * o.colloid(cid)["V"], p0, atol=1e-13)
+    assert changes >= 3  # the solid set did change
