@@ -104,6 +104,15 @@ struct Group {
   Phase ph[4];  // 0 force (diagnostics/export), 1 lb (unused by the step), 2 lc, 3 fused force+lb (step)
   cudaStream_t side = nullptr;   // second stream: link momentum exchange runs beside the Q update
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // Step variant: 0 = fused stress/force/LB kernel; 1 = split: the stress/
+  // force kernel and the LB kernel run concurrently in z slabs on two streams
+  // (LB slab s waits for force slab s only).
+  int variant = 0;
+  int slab = 0;                              // slab thickness in z (0: whole box)
+  cudaStream_t side2 = nullptr;
+  std::vector<cudaEvent_t> ev_slab;
+  cudaEvent_t ev_lb = nullptr;
+  std::vector<int2> chunk_f, chunk_lb;       // (first tile, count) per slab, force and LB phases
   int2* d_chunks = nullptr;
   int nchunks = 0, chunk_cap = 0;
   int2* d_mob = nullptr;        // (box, colloid) of every mobile colloid
@@ -343,6 +352,8 @@ Group* new_group(int prec, void* stream, int nboxes, std::string* err) {
     g->own_stream = true;
   }
   if (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&g->side2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_lb, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     fail(err, LC_ERR_CUDA, "cannot create the side stream");
@@ -378,6 +389,12 @@ void free_group(Group* g) {
   }
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
   if (g->ev_join) cudaEventDestroy(g->ev_join);
+  if (g->side2) {
+    cudaStreamSynchronize(g->side2);
+    cudaStreamDestroy(g->side2);
+  }
+  if (g->ev_lb) cudaEventDestroy(g->ev_lb);
+  for (cudaEvent_t e : g->ev_slab) cudaEventDestroy(e);
   if (g->own_stream) cudaStreamDestroy(g->stream);
   for (lc_lb* h : g->boxes) delete h;
   delete g;
@@ -406,10 +423,13 @@ void tune_file_load() {
   FILE* f = fopen(path, "r");
   if (!f) return;
   long long sig;
-  int prec, v[6];
-  while (fscanf(f, "%lld %d %d %d %d %d %d %d", &sig, &prec, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 8) {
-    std::vector<TileCfg> c(2);
-    for (int k = 0; k < 2; ++k) c[k] = TileCfg{v[3 * k], v[3 * k + 1], v[3 * k + 2]};
+  int prec, v[15];
+  while (fscanf(f, "%lld %d", &sig, &prec) == 2) {
+    bool ok = true;
+    for (int k = 0; k < 15 && ok; ++k) ok = fscanf(f, "%d", &v[k]) == 1;
+    if (!ok) break;
+    std::vector<TileCfg> c(5);
+    for (int k = 0; k < 5; ++k) c[k] = TileCfg{v[3 * k], v[3 * k + 1], v[3 * k + 2]};
     g_tune_cache[TuneKey(sig, prec)] = c;
   }
   fclose(f);
@@ -421,7 +441,7 @@ void tune_file_store(const TuneKey& key, const std::vector<TileCfg>& c) {
   FILE* f = fopen(path, "a");
   if (!f) return;
   fprintf(f, "%lld %d", std::get<0>(key), std::get<1>(key));
-  for (int k = 0; k < 2; ++k) fprintf(f, " %d %d %d", c[k].ty, c[k].zc, c[k].persistent);
+  for (int k = 0; k < 5; ++k) fprintf(f, " %d %d %d", c[k].ty, c[k].zc, c[k].persistent);
   fprintf(f, "\n");
   fclose(f);
 }
@@ -438,51 +458,99 @@ cudaError_t launch_phase(Group* g, int k, int mode, int box = -1) {
 
 // Time every candidate tile shape of each phase on the group's own state (the
 // phase kernels are idempotent between parity flips) and keep the fastest.
+int build_chunks_slab(Group* g);
+int enqueue_split(Group* g, int force_mode);
+
+float time_ms(Group* g, cudaEvent_t e0, cudaEvent_t e1, int reps, int (*fn)(Group*, void*), void* arg, int* rc) {
+  *rc = fn(g, arg);  // warm-up
+  if (*rc) return 1e30f;
+  if (cudaEventRecord(e0, g->stream) != cudaSuccess) return 1e30f;
+  for (int r = 0; r < reps && !*rc; ++r) *rc = fn(g, arg);
+  if (*rc || cudaEventRecord(e1, g->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return ms / reps;
+}
+
+int tune_phase_fn(Group* g, void* arg) {
+  const int k = *static_cast<int*>(arg);
+  const int mode = k == 2 ? LC_RESID : 0;  // no colloid accumulation while tuning
+  CK(launch_phase(g, k, mode), &g->err);
+  return LC_OK;
+}
+int tune_split_fn(Group* g, void*) { return enqueue_split(g, 0); }
+
+// Time every candidate tile shape of each phase kernel on the group's own
+// state (the phase kernels are idempotent between parity flips), then the
+// slab thickness of the split variant, then fused against split, and keep
+// the fastest.
 int autotune_group(Group* g, std::string* desc) {
-  const int zcs[7] = {1, 2, 4, 8, 16, 32, 64};
   const int pers[3] = {0, 2, 4};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), &g->err);
   CK(cudaEventCreate(&e1), &g->err);
   char buf[256];
   std::string out;
-  for (int k : {3, 2}) {
+  int rc = LC_OK;
+  float best_phase[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+  for (int k : {3, 2, 0, 1}) {
     TileCfg best = g->ph[k].cfg;
-    float best_ms = 1e30f;
     const std::vector<int> tys = k == 3 ? std::vector<int>{4, 6, 8} : std::vector<int>{2, 4, 8};
+    const std::vector<int> zcs = k == 1 ? std::vector<int>{1, 2, 4, 8, 16} : std::vector<int>{2, 4, 8, 16, 32, 64};
     for (int ty : tys)
       for (int zc : zcs)
         for (int pp : pers) {
-          if (k == 3 && zc < 2) continue;
           g->ph[k].cfg = TileCfg{ty, zc, pp};
-          if (build_phase(g, k)) return LC_ERR_OOM;
-          const int mode = k == 2 ? LC_RESID : 0;  // no colloid accumulation while tuning
-          CK(launch_phase(g, k, mode), &g->err);  // warm-up
-          CK(cudaEventRecord(e0, g->stream), &g->err);
-          for (int r = 0; r < 3; ++r) CK(launch_phase(g, k, mode), &g->err);
-          CK(cudaEventRecord(e1, g->stream), &g->err);
-          CK(cudaEventSynchronize(e1), &g->err);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (ms < best_ms) {
-            best_ms = ms;
+          if ((rc = build_phase(g, k))) return rc;
+          int kk = k;
+          const float ms = time_ms(g, e0, e1, 3, tune_phase_fn, &kk, &rc);
+          if (rc) return rc;
+          if (ms < best_phase[k]) {
+            best_phase[k] = ms;
             best = g->ph[k].cfg;
           }
         }
     g->ph[k].cfg = best;
-    if (build_phase(g, k)) return LC_ERR_OOM;
-    snprintf(buf, sizeof(buf), "%s:ty=%d,zc=%d,pers=%d(%.1fus) ", k == 3 ? "flb" : "lc", best.ty, best.zc,
-             best.persistent, 1000.f * best_ms / 3.f);
+    if ((rc = build_phase(g, k))) return rc;
+    snprintf(buf, sizeof(buf), "%s:ty=%d,zc=%d,pers=%d(%.1fus) ",
+             k == 3 ? "flb" : (k == 2 ? "lc" : (k == 0 ? "force" : "lb")), best.ty, best.zc, best.persistent,
+             1000.f * best_phase[k]);
     out += buf;
   }
+  // split variant: slab thickness (multiples of both tile depths), 0 = whole box
+  int maxnz = 1;
+  for (lc_lb* h : g->boxes) maxnz = std::max(maxnz, h->grid.nz);
+  const int a = g->ph[0].cfg.zc, b = g->ph[1].cfg.zc;
+  int l = a;
+  while (l % b) l += a;
+  float best_split = 1e30f;
+  int best_slab = 0;
+  for (int m = 1; l * m <= maxnz; m *= 2) {
+    g->slab = l * m;
+    if ((rc = build_chunks_slab(g))) return rc;
+    const float ms = time_ms(g, e0, e1, 3, tune_split_fn, nullptr, &rc);
+    if (rc) return rc;
+    if (ms < best_split) {
+      best_split = ms;
+      best_slab = g->slab;
+    }
+  }
+  g->slab = best_slab;
+  if ((rc = build_chunks_slab(g))) return rc;
+  g->variant = best_split < best_phase[3] ? 1 : 0;
+  snprintf(buf, sizeof(buf), "split(slab=%d,%.1fus) -> %s", best_slab, 1000.f * best_split,
+           g->variant ? "split" : "fused");
+  out += buf;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_tune_cache[tune_key(g)] = {g->ph[3].cfg, g->ph[2].cfg};
+    g_tune_cache[tune_key(g)] = {g->ph[3].cfg, g->ph[2].cfg, g->ph[0].cfg, g->ph[1].cfg,
+                                 TileCfg{g->variant, g->slab, 0}};
     tune_file_store(tune_key(g), g_tune_cache[tune_key(g)]);
   }
   g->tuned = true;
+  g->dirty = true;
   if (desc) *desc = out;
   return LC_OK;
 }
@@ -500,29 +568,104 @@ int maybe_tune(Group* g) {
     if (it != g_tune_cache.end()) {
       g->ph[3].cfg = it->second[0];
       g->ph[2].cfg = it->second[1];
+      g->ph[0].cfg = it->second[2];
+      g->ph[1].cfg = it->second[3];
+      g->variant = it->second[4].ty;
+      g->slab = it->second[4].zc;
       g->tuned = true;
     }
   }
   if (g->tuned) {
-    for (int k : {2, 3})
-      if (build_phase(g, k)) return LC_ERR_OOM;
-    return LC_OK;
+    for (int k = 0; k < 4; ++k)
+      if (int rc = build_phase(g, k)) return rc;
+    return build_chunks_slab(g);
   }
   const char* env = getenv("LCLB_AUTOTUNE");
   if (env && env[0] == '0') {
     g->tuned = true;
-    return LC_OK;
+    return build_chunks_slab(g);
   }
   return autotune_group(g, nullptr);
 }
 
 // ---- one step -----------------------------------------------------------------
+// Slab chunks of the force (phase 0) and LB (phase 1) tile lists: tiles are
+// ordered (box, z, y, x), so the tiles of box b with z0 in [s*slab,
+// (s+1)*slab) are contiguous in both lists.
+int build_chunks_slab(Group* g) {
+  g->chunk_f.clear();
+  g->chunk_lb.clear();
+  const Phase& F = g->ph[0];
+  const Phase& L = g->ph[1];
+  for (size_t b = 0; b < g->boxes.size(); ++b) {
+    const int nz = g->boxes[b]->grid.nz;
+    const int sz = g->slab > 0 ? g->slab : nz;
+    int fi = F.start[b], li = L.start[b];
+    const int fe = F.start[b] + F.count[b], le = L.start[b] + L.count[b];
+    const int zcF = F.cfg.zc, zcL = L.cfg.zc;
+    const int tilesF = F.count[b] / ((nz + zcF - 1) / zcF), tilesL = L.count[b] / ((nz + zcL - 1) / zcL);
+    for (int z = 0; z < nz; z += sz) {
+      const int ze = std::min(nz, z + sz);
+      const int nf = ((ze + zcF - 1) / zcF - (z + zcF - 1) / zcF) * tilesF;
+      const int nl = ((ze + zcL - 1) / zcL - (z + zcL - 1) / zcL) * tilesL;
+      g->chunk_f.push_back(make_int2(fi, nf));
+      g->chunk_lb.push_back(make_int2(li, nl));
+      fi += nf;
+      li += nl;
+    }
+    if (fi != fe || li != le) return fail(&g->err, LC_ERR_STATE, "slab chunks do not cover the tile lists");
+  }
+  while (g->ev_slab.size() < g->chunk_f.size()) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), &g->err);
+    g->ev_slab.push_back(e);
+  }
+  g->dirty = true;
+  return LC_OK;
+}
+
+cudaError_t launch_range(Group* g, int k, int2 range, int mode, cudaStream_t st) {
+  Phase& P = g->ph[k];
+  Launch L;
+  L.boxes = g->d_boxes;
+  L.zc = P.cfg.zc;
+  L.ty = P.cfg.ty;
+  L.stream = st;
+  L.tiles = P.d_tiles + range.x;
+  L.ntiles = range.y;
+  L.grid = P.cfg.persistent ? std::max(1, std::min(range.y, g->nsm * P.cfg.persistent)) : range.y;
+  const int width = k == 0 ? 1 : 4;
+  double* part = P.d_part + (size_t)range.x * width;
+  return k == 0 ? launch_force(g->prec, L, mode, part) : launch_lb(g->prec, L, mode, part);
+}
+
+// Split variant of the force + LB part of a step (see Group::variant).
+int enqueue_split(Group* g, int force_mode) {
+  const size_t n = g->chunk_f.size();
+  for (size_t c = 0; c < n; ++c) {
+    if (g->chunk_f[c].y > 0) CK(launch_range(g, 0, g->chunk_f[c], force_mode, g->stream), &g->err);
+    CK(cudaEventRecord(g->ev_slab[c], g->stream), &g->err);
+  }
+  for (size_t c = 0; c < n; ++c) {
+    CK(cudaStreamWaitEvent(g->side2, g->ev_slab[c], 0), &g->err);
+    if (g->chunk_lb[c].y > 0) CK(launch_range(g, 1, g->chunk_lb[c], 0, g->side2), &g->err);
+  }
+  CK(cudaEventRecord(g->ev_lb, g->side2), &g->err);
+  CK(cudaStreamWaitEvent(g->stream, g->ev_lb, 0), &g->err);
+  return LC_OK;
+}
+
 // One coupled step: fused stress + body force + collide/stream, then the Q
 // update on the main stream and the link momentum exchange on the side
 // stream (both read only what the fused kernel wrote), joined before the
 // colloid update.
 int enqueue_step(Group* g) {
-  CK(launch_phase(g, 3, FORCE_ACC), &g->err);
+  if (g->variant == 1) {
+    int rc = enqueue_split(g, FORCE_ACC);
+    if (rc) return rc;
+  } else {
+    CK(launch_phase(g, 3, FORCE_ACC), &g->err);
+  }
   if (g->nchunks > 0) {
     CK(cudaEventRecord(g->ev_fork, g->stream), &g->err);
     CK(cudaStreamWaitEvent(g->side, g->ev_fork, 0), &g->err);
@@ -605,7 +748,12 @@ int group_profile(Group* g, int n, double* ms) {
   double acc[5] = {0, 0, 0, 0, 0};
   for (int s = 0; s < n; ++s) {
     CK(cudaEventRecord(ev[0], g->stream), &g->err);
-    CK(launch_phase(g, 3, FORCE_ACC), &g->err);
+    if (g->variant == 1) {
+      int rc2 = enqueue_split(g, FORCE_ACC);
+      if (rc2) return rc2;
+    } else {
+      CK(launch_phase(g, 3, FORCE_ACC), &g->err);
+    }
     CK(cudaEventRecord(ev[1], g->stream), &g->err);
     CK(launch_phase(g, 2, LC_RESID), &g->err);
     CK(cudaEventRecord(ev[2], g->stream), &g->err);
