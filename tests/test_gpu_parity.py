@@ -342,3 +342,25 @@ def test_chol128_full_size_fp32_steps(P):
     g.step(3)
     o.step(3)
     compare(g, o, TOL32, ncol=1, radii=[c["a0"]])
+
+
+def test_batched64_full_size_sampled(P):
+    """The 64-box sweep (32^3..96^3, nematic/cholesteric, normal/planar, weak
+    anchoring) advanced together in the launch configuration the bench times;
+    the three smallest boxes are checked against the oracle."""
+    import bench
+    B, specs = bench.build_batch(P, None)
+    B.step(3)
+    order = sorted(range(len(specs)), key=lambda i: specs[i]["grid"][0])[:3]
+    for i in order:
+        b = specs[i]
+        o = oracle.Oracle(*b["grid"], threads=8, **b["params"])
+        ini = b["init"]
+        if ini["kind"] == "helix":
+            o.init_helix(ini["axis"], ini["amp"], ini["seed"])
+        else:
+            o.init_uniaxial(ini["n"], ini["amp"], ini["seed"])
+        c = b["colloids"][0]
+        o.add_colloid(c["X"], c["a0"], c["anchoring"], c["w"])
+        o.step(3)
+        compare(B.boxes[i], o, TOL32, ncol=1, radii=[c["a0"]])
