@@ -133,6 +133,26 @@ def lib(use_torch_allocator: bool = True):
         L.lc_lb_batch_last_error.argtypes = [vp]
         L.lc_lb_batch_last_error.restype = C.c_char_p
         L.lc_lb_autotune.argtypes = [C.POINTER(lc_grid), C.c_int, vp, C.c_char_p, C.c_size_t]
+        # learned warm start (include/lc_nn.h)
+        L.lc_nn_conv3d_fwd.argtypes = [vp, vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                       C.c_int, vp]
+        L.lc_nn_conv3d_dgrad.argtypes = [vp, vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+        L.lc_nn_conv3d_wgrad.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+        L.lc_nn_bias_grad.argtypes = [vp, vp, C.c_int, C.c_int, vp]
+        L.lc_nn_relu_bwd.argtypes = [vp, vp, vp, vp, C.c_size_t, vp]
+        L.lc_nn_cast_bf16.argtypes = [vp, vp, C.c_size_t, vp]
+        L.lc_nn_pool2.argtypes = [vp, vp, C.c_int, C.c_int, vp]
+        L.lc_nn_pool2_bwd.argtypes = [vp, vp, C.c_int, C.c_int, vp]
+        L.lc_nn_up2_concat.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, vp]
+        L.lc_nn_up2_concat_bwd.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, vp]
+        L.lc_nn_mse.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int, C.c_int, C.c_double, vp]
+        L.lc_nn_adam.argtypes = [vp, vp, vp, vp, vp, C.c_size_t, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
+                                 vp]
+        L.lc_nn_pack_input.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, vp, vp, vp, vp, C.c_int, C.c_int,
+                                       vp]
+        L.lc_nn_from_soa.argtypes = [vp, vp, C.c_int, vp]
+        L.lc_nn_to_soa.argtypes = [vp, vp, vp, C.c_int, C.c_int, vp]
+        L.lc_nn_trilinear2.argtypes = [vp, vp, C.c_int, C.c_int, vp]
         if use_torch_allocator:
             _torch_allocator(L)
         _lib = L

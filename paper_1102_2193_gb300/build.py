@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["lclb_kernels.cu", "lclb_api.cu"]
+SOURCES = ["lclb_kernels.cu", "lclb_api.cu", "lcnn_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-Xcompiler", "-ffp-contract=off",
@@ -39,7 +39,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     os.makedirs(OUT, exist_ok=True)
     so = os.path.join(OUT, "liblclb.so")
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(INCLUDE, "lc_lb.h"))
+    headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     objs, procs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

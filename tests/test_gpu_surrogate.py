@@ -1,0 +1,178 @@
+"""Warm-start U-Net kernels against the FP64 numpy reference.
+
+Single kernels are fed BF16-exact inputs, so their only error is FP32
+accumulation (tolerance 1e-5 relative); the whole network carries BF16
+activations (tolerance 3e-2 on the output norm, 5e-2 on each layer's
+gradient norm).
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import nn
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1102_2193_gb300 as P
+    P.lib()
+    return P
+
+
+def bf16_exact(a):
+    return torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def dev16(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda").to(torch.bfloat16)
+
+
+def dev32(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+@pytest.mark.parametrize("cin,cout,taps", [(16, 8, 27), (32, 48, 27), (48, 16, 27), (16, 16, 1), (80, 32, 27)])
+def test_conv_fwd_dgrad_wgrad(P, cin, cout, taps):
+    L = P.lib()
+    rng = np.random.default_rng(cin * 100 + cout + taps)
+    D, H, W = 6, 4, 10
+    x = bf16_exact(rng.standard_normal((D, H, W, cin)))
+    w = bf16_exact(rng.standard_normal((cout, taps, cin)) / np.sqrt(cin * taps))
+    b = rng.standard_normal(cout)
+    y_ref = nn.conv(x, w, b)
+    out = torch.empty((D * H * W, cout), dtype=torch.float32, device="cuda")
+    bias = dev32(b)
+    assert L.lc_nn_conv3d_fwd(ptr(dev16(x)), ptr(dev16(w)), ptr(bias), ptr(out), None, W, H, D, cin, cout, taps, 0,
+                              None) == 0
+    torch.cuda.synchronize()
+    y = out.cpu().numpy().reshape(D, H, W, cout)
+    assert rel(y, y_ref) < 1e-5
+    # ReLU epilogue and BF16 output
+    o16 = torch.empty((D * H * W, cout), dtype=torch.bfloat16, device="cuda")
+    assert L.lc_nn_conv3d_fwd(ptr(dev16(x)), ptr(dev16(w)), ptr(bias), None, ptr(o16), W, H, D, cin, cout, taps, 1,
+                              None) == 0
+    np.testing.assert_allclose(o16.float().cpu().numpy().reshape(D, H, W, cout), np.maximum(y_ref, 0), rtol=1e-2,
+                               atol=1e-2)
+    if cout % 16 == 0:
+        dz = bf16_exact(rng.standard_normal((D, H, W, cout)))
+        dx_ref, dw_ref, _ = nn.conv_bwd(x, w, dz)
+        din = torch.empty((D * H * W, cin), dtype=torch.float32, device="cuda")
+        wt = torch.empty(cout * taps * cin, dtype=torch.bfloat16, device="cuda")
+        assert L.lc_nn_conv3d_dgrad(ptr(dev16(dz)), ptr(dev16(w)), ptr(wt), ptr(din), None, W, H, D, cin, cout, taps,
+                                    None) == 0
+        dw = torch.zeros((cout, taps, cin), dtype=torch.float32, device="cuda")
+        assert L.lc_nn_conv3d_wgrad(ptr(dev16(dz)), ptr(dev16(x)), ptr(dw), W, H, D, cin, cout, taps, None) == 0
+        torch.cuda.synchronize()
+        assert rel(din.cpu().numpy().reshape(D, H, W, cin), dx_ref) < 1e-5
+        assert rel(dw.cpu().numpy(), dw_ref) < 1e-5
+
+
+def test_pool_upsample_kernels(P):
+    L = P.lib()
+    rng = np.random.default_rng(7)
+    S, c1, c2 = 8, 16, 32
+    x = bf16_exact(rng.standard_normal((S, S, S, c1)))
+    out = torch.empty((S**3 // 8, c1), dtype=torch.bfloat16, device="cuda")
+    assert L.lc_nn_pool2(ptr(dev16(x)), ptr(out), S, c1, None) == 0
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(out.float().cpu().numpy().reshape(S // 2, S // 2, S // 2, c1), nn.pool(x), atol=2e-2,
+                               rtol=1e-2)
+    d = rng.standard_normal((S // 2, S // 2, S // 2, c1))
+    din = torch.zeros((S**3, c1), dtype=torch.float32, device="cuda")
+    assert L.lc_nn_pool2_bwd(ptr(dev32(d)), ptr(din), S, c1, None) == 0
+    lo = bf16_exact(rng.standard_normal((S // 2, S // 2, S // 2, c1)))
+    sk = bf16_exact(rng.standard_normal((S, S, S, c2)))
+    u = torch.empty((S**3, c1 + c2), dtype=torch.bfloat16, device="cuda")
+    assert L.lc_nn_up2_concat(ptr(dev16(lo)), ptr(dev16(sk)), ptr(u), S, c1, c2, None) == 0
+    du = rng.standard_normal((S, S, S, c1 + c2))
+    dlo = torch.empty(((S // 2)**3, c1), dtype=torch.float32, device="cuda")
+    dsk = torch.zeros((S**3, c2), dtype=torch.float32, device="cuda")
+    assert L.lc_nn_up2_concat_bwd(ptr(dev32(du)), ptr(dlo), ptr(dsk), S, c1, c2, None) == 0
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(din.cpu().numpy().reshape(S, S, S, c1), nn.pool_bwd(d), rtol=1e-6, atol=1e-7)
+    np.testing.assert_array_equal(u.float().cpu().numpy().reshape(S, S, S, c1 + c2), nn.up_concat(lo, sk))
+    rlo, rsk = nn.up_concat_bwd(du, c1)
+    np.testing.assert_allclose(dlo.cpu().numpy().reshape(rlo.shape), rlo, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(dsk.cpu().numpy().reshape(rsk.shape), rsk, rtol=1e-6, atol=1e-7)
+
+
+def _unet_case(S=8, seed=11):
+    rng = np.random.default_rng(seed)
+    params = {n: [bf16_exact(rng.standard_normal((co, t, ci)) * np.sqrt(2.0 / (ci * t))),
+                  rng.standard_normal(co) * 0.05] for n, ci, co, t, r, lvl in nn.LAYERS}
+    params["c0a"][0][:, :, 9:] = 0.0
+    solid = np.where(rng.uniform(size=(S, S, S)) < 0.15, 0.0, -1.0)
+    q = rng.uniform(-0.3, 0.3, size=(5, S, S, S))
+    target = rng.uniform(-0.3, 0.3, size=(S, S, S, 5))
+    return params, solid, q, target
+
+
+def test_unet_forward_and_gradients_match_reference(P):
+    from paper_1102_2193_gb300.surrogate import UNet
+    S = 8
+    params, solid, q, target = _unet_case(S)
+    net = UNet(S=S, seed=0)
+    net.load({n: {"w": v[0].astype(np.float32), "b": v[1].astype(np.float32)} for n, v in params.items()})
+    net.set_input(torch.tensor(solid.reshape(-1), device="cuda"), torch.tensor(q.reshape(5, -1), device="cuda"),
+                  6.0, 16.0, 0.02)
+    net.set_target(torch.tensor(np.moveaxis(target, -1, 0).reshape(5, -1).copy(), device="cuda"))
+    net.forward()
+    Lg = net.loss_and_grad()
+    net.backward()
+    torch.cuda.synchronize()
+    x = nn.pack_input(solid, q, 6.0, 16.0, 0.02)
+    y, a = nn.forward(params, bf16_exact(x))
+    fluid = (solid < 0).astype(float)
+    Lr, dy = nn.loss(y, np.moveaxis(q, 0, -1), target, fluid)
+    g = nn.backward(params, a, dy)
+    assert rel(net.y.cpu().numpy().reshape(S, S, S, 16), y) < 3e-2
+    assert abs(Lg - Lr) < 3e-2 * Lr
+    for n in params:
+        assert rel(net.params[n]["gw"].cpu().numpy(), g[f"{n}_w"]) < 5e-2, n
+        assert rel(net.params[n]["gb"].cpu().numpy(), g[f"{n}_b"]) < 5e-2, n
+
+
+def test_training_reduces_the_loss(P):
+    from paper_1102_2193_gb300.surrogate import UNet
+    S = 16
+    _, solid, q, target = _unet_case(S, seed=5)
+    net = UNet(S=S, seed=1)
+    net.set_input(torch.tensor(solid.reshape(-1), device="cuda"), torch.tensor(q.reshape(5, -1), device="cuda"),
+                  6.0, 16.0, 0.02)
+    net.set_target(torch.tensor(np.moveaxis(target, -1, 0).reshape(5, -1).copy(), device="cuda"))
+    losses = []
+    for _ in range(150):
+        net.forward()
+        losses.append(net.loss_and_grad())
+        net.backward()
+        net.adam(lr=3e-3)
+    # the target is noise: fitting it is slow, but the loss must fall steadily
+    assert losses[-1] < 0.6 * losses[0], losses[::25]
+
+
+def test_trilinear_upsampling_of_smooth_field(P):
+    L = P.lib()
+    S = 16
+    z, y, x = np.meshgrid(np.arange(S), np.arange(S), np.arange(S), indexing="ij")
+    f = np.stack([np.cos(2 * np.pi * (x + 0.5) / S) * np.sin(2 * np.pi * (z + 0.5) / S)] * 5)  # cell-centred
+    a = torch.tensor(f.reshape(5, -1).copy(), device="cuda")
+    b = torch.empty((5, 8 * S**3), dtype=torch.float64, device="cuda")
+    assert L.lc_nn_trilinear2(ptr(a), ptr(b), S, 5, None) == 0
+    torch.cuda.synchronize()
+    F = 2 * S
+    Z, Y, X = np.meshgrid(np.arange(F), np.arange(F), np.arange(F), indexing="ij")
+    ref = np.cos(2 * np.pi * (X + 0.5) / F) * np.sin(2 * np.pi * (Z + 0.5) / F)
+    assert np.abs(b.cpu().numpy()[0].reshape(F, F, F) - ref).max() < 0.03
