@@ -1,0 +1,206 @@
+"""Warm-started relaxation of a colloid in a cholesteric (Sec. 3.2 statics).
+
+1. ``relaxed_dataset``: boxes with one normally anchored colloid (radius R,
+   pitch p, anchoring strength w from a seeded generator) are relaxed from the
+   helix by the lattice method itself, many boxes at once (``lc_lb`` batch);
+   the inputs (solid map, helix Q) and the relaxed Q stay on the device.
+2. ``train``: the U-Net of ``surrogate`` is fitted to them with its own
+   forward/backward kernels and Adam.
+3. ``propose`` / ``compare``: the network's Q (trilinearly upsampled when the
+   target box is twice the network's) replaces the helix as the start, and
+   the plain relaxation, which stays the judge and the fallback, is run from
+   both starts; steps, wall time, residual and free energy are reported.
+
+The relaxation runs with the flow frozen (u = 0): the statics do not depend on
+it, and with the paper's constants the coupled flow at tau = 2.5 is unstable.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import LC_FP32, LC_FP64, LC_NORMAL, LC_Q, Batch, Solver
+from .surrogate import UNet, solver_fields, upsample2
+
+PAPER = dict(rho0=1.0, tau=2.5, A0=1.0, gamma=3.0, K=0.065, xi=0.7, Gamma=0.5)
+
+
+def geometries(n: int, S: int, seed: int) -> list:
+    """n seeded (R, pitch, w) with p in {16, 20, ..., 32}, R/p in [0.1, 0.6], w in [0.005, 0.05]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        p = float(rng.choice([16, 20, 24, 28, 32]))
+        R = float(rng.uniform(0.1, 0.6) * p)
+        if not 3.0 <= R <= S / 4:
+            continue
+        out.append(dict(R=round(R, 3), pitch=p, w=float(rng.uniform(0.005, 0.05))))
+    return out
+
+
+def _params(spec):
+    return dict(PAPER, q0=2.0 * math.pi / spec["pitch"], flow=False)
+
+
+def _setup(box, spec, S):
+    box.init_helix(2, 0.0, 0)
+    c = (S - 1) / 2.0
+    box.add_colloid((c, c, c), spec["R"], LC_NORMAL, spec["w"])
+
+
+def relaxed_dataset(specs, S, steps, torch, precision=LC_FP32, chunk=32):
+    """Inputs and relaxed targets, all as FP64 device tensors."""
+    data = []
+    for k in range(0, len(specs), chunk):
+        part = specs[k:k + chunk]
+        B = Batch([dict(grid=(S, S, S), params=_params(sp)) for sp in part], precision=precision)
+        for box, sp in zip(B.boxes, part):
+            _setup(box, sp, S)
+        inputs = [solver_fields(box, torch) for box in B.boxes]
+        B.step(steps)
+        for box, sp, (solid, q0) in zip(B.boxes, part, inputs):
+            q = torch.empty((5, S**3), dtype=torch.float64, device="cuda")
+            box.get_fields(LC_Q, q)
+            data.append(dict(spec=sp, solid=solid, q0=q0, target=q))
+        B.close()
+    return data
+
+
+def train(net: UNet, data, epochs: int, lr: float = 2e-3, seed: int = 0, log=None):
+    rng = np.random.default_rng(seed)
+    hist = []
+    for ep in range(epochs):
+        tot = 0.0
+        for i in rng.permutation(len(data)):
+            d = data[i]
+            net.set_input(d["solid"], d["q0"], d["spec"]["R"], d["spec"]["pitch"], d["spec"]["w"])
+            net.set_target(d["target"])
+            net.forward()
+            tot += net.loss_and_grad()
+            net.backward()
+            net.adam(lr=lr * (0.5 ** (ep / max(1, epochs // 3))))
+        hist.append(tot / len(data))
+        if log:
+            log(f"epoch {ep}: loss {hist[-1]:.3e}")
+    return hist
+
+
+def evaluate_loss(net: UNet, data) -> float:
+    tot = 0.0
+    for d in data:
+        net.set_input(d["solid"], d["q0"], d["spec"]["R"], d["spec"]["pitch"], d["spec"]["w"])
+        net.set_target(d["target"])
+        net.forward()
+        tot += net.loss_and_grad(grad=False)
+    return tot / len(data)
+
+
+def propose(net: UNet, spec, S_target: int, torch):
+    """Network Q for a box of size S_target (= net.S or 2 net.S); in the
+    second case the network sees the geometry halved and its output is
+    trilinearly upsampled (the 5-component storage stays traceless)."""
+    scale = S_target // net.S
+    s = dict(spec, R=spec["R"] / scale, pitch=spec["pitch"] / scale)
+    tmp = Solver(net.S, net.S, net.S, precision=LC_FP32, **_params(s))
+    _setup(tmp, s, net.S)
+    solid, q0 = solver_fields(tmp, torch)
+    net.set_input(solid, q0, s["R"], s["pitch"], s["w"])
+    net.forward()
+    q = net.predict_soa()
+    tmp.close()
+    if scale == 2:
+        q = upsample2(q, net.S, torch)
+    return q
+
+
+def relax_from(spec, S, q_start, tol_fp32, tol, torch, max_steps=2_000_000, check=1000):
+    """Relax from q_start (None: the helix) in FP32 until tol_fp32; then, if
+    tol is given, hand the state to FP64 and continue until tol.  Returns
+    steps, wall time, residuals and the free energy."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s32 = Solver(S, S, S, precision=LC_FP32, **_params(spec))
+    _setup(s32, spec, S)
+    if q_start is not None:
+        s32.set_fields(LC_Q, q_start)
+    n32, r32 = s32.relax(tol=tol_fp32, max_steps=max_steps, check_every=check)
+    t32 = time.perf_counter() - t0
+    out = dict(steps_fp32=n32, resid_fp32=r32, time_fp32=t32, steps_fp64=0, resid=r32)
+    if tol is None:
+        d = s32.diag()
+        s32.close()
+        out.update(time=t32, free_energy=d["free_energy"], n_defect=d["n_defect"])
+        return out
+    q = torch.empty((5, S**3), dtype=torch.float64, device="cuda")
+    s32.get_fields(LC_Q, q)
+    s32.close()
+    s64 = Solver(S, S, S, precision=LC_FP64, **_params(spec))
+    _setup(s64, spec, S)
+    s64.set_fields(LC_Q, q)
+    n64, r64 = s64.relax(tol=tol, max_steps=max_steps, check_every=check)
+    d = s64.diag()
+    s64.close()
+    out.update(steps_fp64=n64, resid=r64, time=time.perf_counter() - t0, free_energy=d["free_energy"],
+               n_defect=d["n_defect"])
+    return out
+
+
+def compare(net: UNet, spec, S, torch, tol_fp32=3e-8, tol=1e-8, max_steps=2_000_000):
+    q_warm = propose(net, spec, S, torch)
+    plain = relax_from(spec, S, None, tol_fp32, tol, torch, max_steps)
+    warm = relax_from(spec, S, q_warm, tol_fp32, tol, torch, max_steps)
+    use_warm = warm["free_energy"] <= plain["free_energy"] + 1e-4 * abs(plain["free_energy"])
+    return dict(spec=spec, S=S, plain=plain, warm=warm, warm_accepted=bool(use_warm),
+                speedup_steps=(plain["steps_fp32"] + plain["steps_fp64"]) /
+                max(1, warm["steps_fp32"] + warm["steps_fp64"]),
+                speedup_time=plain["time"] / max(warm["time"], 1e-9),
+                free_energy_rel=(warm["free_energy"] - plain["free_energy"]) / abs(plain["free_energy"]))
+
+
+def main(argv=None):
+    """Train on relaxed boxes and compare warm-started with plain relaxation; prints one JSON line."""
+    import argparse
+    import json
+
+    import torch
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--S", type=int, default=64)
+    ap.add_argument("--train", type=int, default=48)
+    ap.add_argument("--hold", type=int, default=8)
+    ap.add_argument("--relax-steps", type=int, default=30000)
+    ap.add_argument("--epochs", type=int, default=15)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--tol32", type=float, default=3e-8)
+    ap.add_argument("--tol64", type=float, default=None)
+    ap.add_argument("--eval", type=int, default=2, help="held-out geometries compared at S")
+    ap.add_argument("--big", action="store_true", help="also compare at 2S: R = 12, p = 32")
+    ap.add_argument("--seed", type=int, default=1000)
+    a = ap.parse_args(argv)
+    t0 = time.perf_counter()
+    specs = geometries(a.train + a.hold, a.S, a.seed)
+    data = relaxed_dataset(specs, a.S, a.relax_steps, torch)
+    t_data = time.perf_counter() - t0
+    net = UNet(S=a.S, seed=a.seed)
+    t1 = time.perf_counter()
+    hist = train(net, data[:a.train], a.epochs, a.lr, log=print)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    res = dict(n_params=net.n_params(), data_s=t_data, train_s=t_train, train_loss=hist,
+               holdout_loss=evaluate_loss(net, data[a.train:]),
+               holdout_loss_identity=None, cases=[])
+    # the loss of the plain helix start on the held-out set (network output zero)
+    zero = UNet(S=a.S, seed=a.seed)
+    res["holdout_loss_identity"] = evaluate_loss(zero, data[a.train:])
+    for sp in specs[a.train:a.train + a.eval]:
+        res["cases"].append(compare(net, sp, a.S, torch, a.tol32, a.tol64))
+    if a.big:
+        res["cases"].append(compare(net, dict(R=12.0, pitch=32.0, w=0.02), 2 * a.S, torch, a.tol32, a.tol64))
+    print(json.dumps(res, default=float), flush=True)
+    return res
+
+
+if __name__ == "__main__":
+    main()

@@ -176,3 +176,24 @@ def test_trilinear_upsampling_of_smooth_field(P):
     Z, Y, X = np.meshgrid(np.arange(F), np.arange(F), np.arange(F), indexing="ij")
     ref = np.cos(2 * np.pi * (X + 0.5) / F) * np.sin(2 * np.pi * (Z + 0.5) / F)
     assert np.abs(b.cpu().numpy()[0].reshape(F, F, F) - ref).max() < 0.03
+
+
+def test_warm_start_pipeline_small(P):
+    """Dataset by batched relaxation, a short training, then plain and warm
+    starts both relaxed to the same tolerance: the network's proposal must not
+    change the relaxed state (same free energy, same defect count)."""
+    from paper_1102_2193_gb300 import warmstart as ws
+    from paper_1102_2193_gb300.surrogate import UNet
+    S = 16
+    specs = ws.geometries(4, S, seed=3)
+    assert all(3.0 <= s["R"] <= S / 4 for s in specs)
+    data = ws.relaxed_dataset(specs, S, 400, torch)
+    assert len(data) == 4 and all(torch.isfinite(d["target"]).all() for d in data)
+    net = UNet(S=S, seed=2)
+    hist = ws.train(net, data[:3], epochs=4, lr=3e-3)
+    assert hist[-1] < hist[0]
+    res = ws.compare(net, specs[3], S, torch, tol_fp32=1e-5, tol=None, max_steps=200_000)
+    for k in ("plain", "warm"):
+        assert res[k]["resid"] <= 1e-5
+    assert abs(res["free_energy_rel"]) < 1e-3
+    assert res["plain"]["n_defect"] == res["warm"]["n_defect"]
