@@ -89,6 +89,7 @@ typedef struct {
   double M, I;
   double Fh[3], Th[3], Flc[3], Tlc[3]; /* forces and torques of the last step */
   double imp[3], aimp[3];              /* momentum / angular momentum received */
+  double zv[3][3], zw[3][3];           /* link drag tensors of the last step (see colloid_update) */
 } ocolloid;
 
 typedef struct {
@@ -686,6 +687,10 @@ static void collide_stream(oracle* o) {
   ksum Fh[OMAXC][3], Th[OMAXC][3];
   memset(Fh, 0, sizeof(Fh));
   memset(Th, 0, sizeof(Th));
+  for (int c = 0; c < o->ncol; ++c) {
+    memset(o->col[c].zv, 0, sizeof(o->col[c].zv));
+    memset(o->col[c].zw, 0, sizeof(o->col[c].zw));
+  }
   for (long k = 0; k < NQ * N; ++k) o->f[k] = 0.0;
   for (int z = 0; z < o->nz; ++z)
     for (int y = 0; y < o->ny; ++y)
@@ -717,6 +722,17 @@ static void collide_stream(oracle* o) {
               kadd(&Fh[c][a], dp[a]);
               kadd(&Th[c][a], t[a]);
             }
+            /* the part of dp linear in the rigid velocity is
+             * -6 w rho0 c (c.(V + Omega x r)); its V-V and Omega-Omega
+             * coefficients (c c and (r x c)(r x c), times 6 w rho0) */
+            double rc[3] = {r[1] * CV[q][2] - r[2] * CV[q][1], r[2] * CV[q][0] - r[0] * CV[q][2],
+                            r[0] * CV[q][1] - r[1] * CV[q][0]};
+            double zk = 6.0 * WQ(q) * o->rho0;
+            for (int a = 0; a < 3; ++a)
+              for (int b = 0; b < 3; ++b) {
+                o->col[c].zv[a][b] += zk * CV[q][a] * CV[q][b];
+                o->col[c].zw[a][b] += zk * rc[a] * rc[b];
+              }
           }
         }
       }
@@ -806,9 +822,43 @@ static void rediscretise(oracle* o) {
       for (int a = 0; a < 3; ++a) o->col[c].V[a] += dpc[c][a] / o->col[c].M;
 }
 
-/* Colloid update, explicit ("molecular dynamics-like", Sec. 2.2):
- *   V += (F_hyd + F_LC + F_ext)/M,  Omega += (T_hyd + T_LC)/I,  X += V,
- * M = rho0 (4/3) pi a0^3 (neutrally buoyant), I = (2/5) M a0^2. */
+/* x = A^{-1} b for a 3x3 matrix: Gaussian elimination with partial pivoting. */
+static void solve3(const double A_in[3][3], const double b_in[3], double x[3]) {
+  double A[3][4];
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) A[a][b] = A_in[a][b];
+    A[a][3] = b_in[a];
+  }
+  for (int k = 0; k < 3; ++k) {
+    int p = k;
+    for (int r = k + 1; r < 3; ++r)
+      if (fabs(A[r][k]) > fabs(A[p][k])) p = r;
+    for (int cidx = 0; cidx < 4; ++cidx) {
+      double t = A[k][cidx];
+      A[k][cidx] = A[p][cidx];
+      A[p][cidx] = t;
+    }
+    for (int r = k + 1; r < 3; ++r) {
+      double m = A[r][k] / A[k][k];
+      for (int cidx = k; cidx < 4; ++cidx) A[r][cidx] -= m * A[k][cidx];
+    }
+  }
+  for (int k = 2; k >= 0; --k) {
+    double v = A[k][3];
+    for (int cidx = k + 1; cidx < 3; ++cidx) v -= A[k][cidx] * x[cidx];
+    x[k] = v / A[k][k];
+  }
+}
+
+/* Colloid update ("molecular dynamics-like", Sec. 2.2), implicit in the
+ * velocity-dependent part of the link force: the link momentum exchange is
+ * F_hyd = F0 - zv V - (cross term in Omega), zv = sum over links of
+ * 6 w rho0 c c; taking the zv V part at the new velocity,
+ *   (M + zv) V' = M V + (F_hyd + zv V) + F_LC + F_ext,
+ * i.e. V' = V + (M + zv)^{-1} (F_hyd + F_LC + F_ext), and likewise
+ * Omega' = Omega + (I + zw)^{-1} (T_hyd + T_LC), zw = sum 6 w rho0 (r x c)(r x c);
+ * X += V'.  M = rho0 (4/3) pi a0^3 (neutrally buoyant), I = (2/5) M a0^2.
+ * With no links (flow off) this is the explicit update. */
 static void colloid_update(oracle* o) {
   int moved = 0;
   for (int c = 0; c < o->ncol; ++c) {
@@ -818,9 +868,20 @@ static void colloid_update(oracle* o) {
       C->aimp[a] += C->Th[a] + C->Tlc[a];
     }
     if (!C->mobile) continue;
+    double Av[3][3], Aw[3][3], bv[3], bw[3], dv[3], dw[3];
     for (int a = 0; a < 3; ++a) {
-      C->V[a] += (C->Fh[a] + C->Flc[a] + C->Fext[a]) / C->M;
-      C->W[a] += (C->Th[a] + C->Tlc[a]) / C->I;
+      for (int b = 0; b < 3; ++b) {
+        Av[a][b] = C->zv[a][b] + (a == b ? C->M : 0.0);
+        Aw[a][b] = C->zw[a][b] + (a == b ? C->I : 0.0);
+      }
+      bv[a] = C->Fh[a] + C->Flc[a] + C->Fext[a];
+      bw[a] = C->Th[a] + C->Tlc[a];
+    }
+    solve3(Av, bv, dv);
+    solve3(Aw, bw, dw);
+    for (int a = 0; a < 3; ++a) {
+      C->V[a] += dv[a];
+      C->W[a] += dw[a];
     }
     for (int a = 0; a < 3; ++a) {
       C->X[a] += C->V[a];

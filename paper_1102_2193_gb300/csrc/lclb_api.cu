@@ -311,11 +311,12 @@ int make_box(Group* g, const lc_grid* G, const lc_params* p, lc_lb* h) {
   }
   B.u = galloc(g, 3 * N * ts);
   B.F = galloc(g, 3 * N * ts);
+  B.H = galloc(g, 5 * N * ts);
   B.mask = (uint8_t*)galloc(g, N);
   B.col = (DevColloid*)galloc(g, sizeof(DevColloid) * MAXCOL);
   B.st = (DevState*)galloc(g, sizeof(DevState));
   B.nlinks = (int*)galloc(g, sizeof(int));
-  if (!B.f[0] || !B.f[1] || !B.Q[0] || !B.Q[1] || !B.u || !B.F || !B.mask || !B.col || !B.st || !B.nlinks)
+  if (!B.f[0] || !B.f[1] || !B.Q[0] || !B.Q[1] || !B.u || !B.F || !B.H || !B.mask || !B.col || !B.st || !B.nlinks)
     return fail(&h->err, LC_ERR_OOM, "device allocation failed for a %dx%dx%d box", G->nx, G->ny, G->nz);
   cudaStream_t s = g->stream;
   for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(B.f[k], 0, NQ * N * ts, s), &h->err);

@@ -56,7 +56,7 @@ struct DevColloid {
   double a0, w, M, I;
   double Fext[3];
   int anchoring, mobile, strong, pad;
-  double acc[12];
+  double acc[24];  // step sums: F_hyd, T_hyd, F_lc, T_lc, then the link drag tensors zv, zw (6 each, xx xy xz yy yz zz)
   double Fh[3], Th[3], Flc[3], Tlc[3];
   double imp[3], aimp[3];
   double rdp[3];  // momentum exchanged by the running re-discretisation
@@ -83,6 +83,7 @@ struct DevBox {
   void* Q[2];
   void* u;
   void* F;
+  void* H;              // molecular field of the current Q at fluid nodes (5 comps), written by the stress kernels
   uint8_t* mask;
   DevColloid* col;
   DevState* st;

@@ -57,9 +57,10 @@ __device__ void block_sum(double v[NV], double* sred, bool is_max_last = false) 
 }
 
 // Add per-lane contributions v[0..5] (for colloid id c, -1: none) into
-// acc[off..off+5] of each colloid with one FP64 atomic per (warp, colloid,
+// acc[off..off+NV-1] of each colloid with one FP64 atomic per (warp, colloid,
 // component).  Must be called by all 32 lanes of a converged warp.
-__device__ __forceinline__ void warp_flush_colloid(DevColloid* col, int c, double v[6], int off) {
+template <int NV = 6>
+__device__ __forceinline__ void warp_flush_colloid(DevColloid* col, int c, const double* v, int off) {
   unsigned pend = __ballot_sync(0xffffffffu, c >= 0);
   const int lane = threadIdx.x & 31;
   while (pend) {
@@ -67,7 +68,7 @@ __device__ __forceinline__ void warp_flush_colloid(DevColloid* col, int c, doubl
     const int cc = __shfl_sync(0xffffffffu, c, leader);
     const bool mine = (c == cc);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < NV; ++k) {
       const double t = warp_sum(mine ? v[k] : 0.0);  // total lands in lane 0
       if (lane == 0 && t != 0.0) atomicAdd(&col[cc].acc[off + k], t);
     }
@@ -87,10 +88,12 @@ __device__ __forceinline__ void load_box(DevBox& sb, const DevBox* boxes, int b)
 // ---------------------------------------------------------------------------
 // Stress P (9 comps) of fluid node (gx,gy,kk) into sP[c*HP] (c = 0..8); the
 // node's mask byte decides fluid/solid.  Returns the flag stored with it:
-// 0 fluid, colloid id + 1, or WALLFLAG.
+// 0 fluid, colloid id + 1, or WALLFLAG.  When hout is non-null (an interior
+// position of the tile) the molecular field H is also stored there, for the
+// Q update of the same step.
 template <typename T>
 __device__ __forceinline__ uint8_t stress_at(const DevBox& B, const PhysT<T>& PP, const T* __restrict__ Q, int gx,
-                                             int gy, int kk, T* sP, int HP, bool fe, double* fe_acc) {
+                                             int gy, int kk, T* sP, int HP, bool fe, double* fe_acc, T* hout) {
   const int i = gx + B.nx * (gy + B.ny * kk);
   const uint8_t m = B.mask[i];
   const uint8_t flag = m & IDMASK;
@@ -101,6 +104,10 @@ __device__ __forceinline__ uint8_t stress_at(const DevBox& B, const PhysT<T>& PP
   lc_node<T, true>(PP, qi, qn, h, p, &fp);
 #pragma unroll
   for (int c = 0; c < 9; ++c) sP[c * HP] = p[c];
+  if (hout) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) hout[(size_t)c * B.N + i] = h[c];
+  }
   if (fe) *fe_acc += (double)fp + surf;
   return 0;
 }
@@ -194,9 +201,9 @@ __global__ void __launch_bounds__(TX * TY) k_force(const DevBox* __restrict__ bo
         if (hx > vx + 1 || hy > vy + 1) continue;
         uint8_t flag = WALLFLAG;
         if (!wallplane) {
-          const bool interior = (mode & FORCE_FE) && hx >= 1 && hx <= vx && hy >= 1 && hy <= vy && k >= z0 && k < zend;
+          const bool inner = hx >= 1 && hx <= vx && hy >= 1 && hy <= vy && k >= z0 && k < zend;
           flag = stress_at(B, PP, Q, wrapn(x0 - 1 + hx, nx), wrapn(y0 - 1 + hy, ny), kk, sP + slot * 9 * HP + pidx,
-                           HP, interior, &fe_acc);
+                           HP, inner && (mode & FORCE_FE), &fe_acc, inner ? static_cast<T*>(B.H) : (T*)nullptr);
         }
         sFl[slot * HP + pidx] = flag;
       }
@@ -434,8 +441,11 @@ __global__ void __launch_bounds__(32 * (BY + 3), (sizeof(T) == 4 && BY <= 4) ? 2
         const bool wallplane = B.wall_z && (k < 0 || k >= nz);
         const int kk = B.wall_z ? k : wrapn(k, nz);
         double dummy = 0.0;
+        const bool inner = hx >= 1 && hx <= vx && hy >= 1 && hy <= vy && k >= z0 && k < zend;
         sFl[slot * HP + pidx] =
-            wallplane ? WALLFLAG : stress_at(B, PP, Q, gx, gy, kk, sP + slot * 9 * HP + pidx, HP, false, &dummy);
+            wallplane ? WALLFLAG
+                      : stress_at(B, PP, Q, gx, gy, kk, sP + slot * 9 * HP + pidx, HP, false, &dummy,
+                                  inner ? static_cast<T*>(B.H) : (T*)nullptr);
       }
       __syncthreads();
       if (k >= z0 + 1 && myint) {
@@ -492,9 +502,16 @@ __global__ void __launch_bounds__(TX * TY) k_lc(const DevBox* __restrict__ boxes
         const int i = x + nx * (y + ny * z);
         const uint8_t m = B.mask[i];
         if (m & IDMASK) continue;
+        // H of this node was stored by the stress kernel of this step; Q of the
+        // fluid face neighbours is needed only for the advective fluxes (zero
+        // across solid faces), so no surface values are formed here
+        const T* __restrict__ Hb = static_cast<const T*>(B.H);
         T qi[5], qn[6][5], h[5];
-        gather_q(B, Q, x, y, z, i, m, qi, qn, nullptr);
-        lc_node<T, false>(PP, qi, qn, h, nullptr, nullptr);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          qi[c] = ldg(Q + (size_t)c * N + i);
+          h[c] = Hb[(size_t)c * N + i];
+        }
         int nb[6], zz[2];
         face_neighbours(B, x, y, z, nb, zz);
         T ui[3], un[6][3];
@@ -507,6 +524,8 @@ __global__ void __launch_bounds__(TX * TY) k_lc(const DevBox* __restrict__ boxes
           fl[d] = j >= 0 && (!(m & NEAR) || (B.mask[j] & IDMASK) == 0);
 #pragma unroll
           for (int a = 0; a < 3; ++a) un[d][a] = j >= 0 ? ldg(U + (size_t)a * N + j) : T(0);
+#pragma unroll
+          for (int c = 0; c < 5; ++c) qn[d][c] = fl[d] ? ldg(Q + (size_t)c * N + j) : T(0);
         }
         // velocity gradient W_ab = d_b u_a
         T W[3][3];
@@ -598,7 +617,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_links(const DevBox* __restrict__ boxes, const int2* __restrict__ chunks,
                                                int nchunks) {
   __shared__ DevBox B;
-  __shared__ double sblk[6];
+  __shared__ double sblk[18];
   __shared__ int sc0;
   const int tid = threadIdx.x;
   for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
@@ -608,9 +627,13 @@ __global__ void __launch_bounds__(256) k_links(const DevBox* __restrict__ boxes,
     const int nl = *B.nlinks;
     const int l = cd.y + tid;
     int my_c = -1;
-    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    bool mob = false;
+    // dp (3), torque (3), then for mobile colloids the drag tensors zv, zw (6 + 6)
+    double v[18];
+#pragma unroll
+    for (int k = 0; k < 18; ++k) v[k] = 0.0;
     // the chunk's first colloid is summed in shared memory (links are sorted by colloid)
-    if (tid < 6) sblk[tid] = 0.0;
+    if (tid < 18) sblk[tid] = 0.0;
     if (tid == 0) sc0 = (cd.y < nl && cd.y < B.nlinks_cap) ? (int)B.link_col[cd.y] : -1;
     __syncthreads();
     if (l < nl && l < B.nlinks_cap) {
@@ -643,27 +666,58 @@ __global__ void __launch_bounds__(256) k_links(const DevBox* __restrict__ boxes,
         v[a] = dp[a];
         v[3 + a] = tq[a];
       }
+      mob = C.mobile != 0;
+      if (mob) {
+        // the part of dp linear in the rigid velocity, -6 w rho0 c (c.(V + W x d)):
+        // coefficients 6 w rho0 c c (V-V) and 6 w rho0 (d x c)(d x c) (W-W)
+        const double zk = 6.0 * w * B.p.rho0;
+        const double cc[3] = {(double)qx, (double)qy, (double)qz};
+        const double rc[3] = {d[1] * cc[2] - d[2] * cc[1], d[2] * cc[0] - d[0] * cc[2], d[0] * cc[1] - d[1] * cc[0]};
+        const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          v[6 + k] = zk * cc[ia[k]] * cc[ib[k]];
+          v[12 + k] = zk * rc[ia[k]] * rc[ib[k]];
+        }
+      }
     }
     const int c0 = sc0;
     const bool main = (my_c == c0) && c0 >= 0;
     const bool warp_main = __all_sync(0xffffffffu, main || my_c < 0);
+    const bool warp_mob = __any_sync(0xffffffffu, mob);
     if (warp_main) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
+      for (int k = 0; k < 18; ++k) {
+        if (k >= 6 && !warp_mob) break;
         const double t = warp_sum(v[k]);
         if ((tid & 31) == 0 && t != 0.0) atomicAdd(&sblk[k], t);
       }
     } else {
-      warp_flush_colloid(B.col, my_c, v, 0);
+      warp_flush_colloid<6>(B.col, my_c, v, 0);
+      if (warp_mob) warp_flush_colloid<12>(B.col, mob ? my_c : -1, v + 6, 12);
     }
     __syncthreads();
-    if (tid < 6 && c0 >= 0 && sblk[tid] != 0.0) atomicAdd(&B.col[c0].acc[tid], sblk[tid]);
+    if (tid < 18 && c0 >= 0 && sblk[tid] != 0.0) atomicAdd(&B.col[c0].acc[tid < 6 ? tid : tid + 6], sblk[tid]);
   }
 }
 
+// x = A^{-1} b for a symmetric 3x3 A given as (xx, xy, xz, yy, yz, zz) plus
+// s on the diagonal (adjugate over determinant; A is positive definite).
+__device__ void solve_sym3(const double* a, double s, const double* b, double* x) {
+  const double m00 = a[0] + s, m01 = a[1], m02 = a[2], m11 = a[3] + s, m12 = a[4], m22 = a[5] + s;
+  const double c00 = m11 * m22 - m12 * m12, c01 = m02 * m12 - m01 * m22, c02 = m01 * m12 - m02 * m11;
+  const double c11 = m00 * m22 - m02 * m02, c12 = m01 * m02 - m00 * m12, c22 = m00 * m11 - m01 * m01;
+  const double det = m00 * c00 + m01 * c01 + m02 * c02;
+  x[0] = (c00 * b[0] + c01 * b[1] + c02 * b[2]) / det;
+  x[1] = (c01 * b[0] + c11 * b[1] + c12 * b[2]) / det;
+  x[2] = (c02 * b[0] + c12 * b[1] + c22 * b[2]) / det;
+}
+
 // ---------------------------------------------------------------------------
-// k_colloid: explicit colloid update ("molecular dynamics-like step") and the
-// end-of-step parity flip.  One block per box, one thread per colloid.
+// k_colloid: colloid update ("molecular dynamics-like step", Sec. 2.2) and the
+// end-of-step parity flip.  One block per box, one thread per colloid.  The
+// velocity-dependent part of the link force is taken at the new velocity:
+// V' = V + (M + zv)^{-1} (F_hyd + F_lc + F_ext), W' = W + (I + zw)^{-1} (T_hyd + T_lc).
 // ---------------------------------------------------------------------------
 __global__ void k_colloid(DevBox* __restrict__ boxes, int nboxes) {
   const int b = blockIdx.x;
@@ -685,9 +739,15 @@ __global__ void k_colloid(DevBox* __restrict__ boxes, int nboxes) {
       C.Wb[a] = C.W[a];
     }
     if (C.mobile) {
+      const double fv[3] = {C.Fh[0] + C.Flc[0] + C.Fext[0], C.Fh[1] + C.Flc[1] + C.Fext[1],
+                            C.Fh[2] + C.Flc[2] + C.Fext[2]};
+      const double tv[3] = {C.Th[0] + C.Tlc[0], C.Th[1] + C.Tlc[1], C.Th[2] + C.Tlc[2]};
+      double dv[3], dw[3];
+      solve_sym3(C.acc + 12, C.M, fv, dv);
+      solve_sym3(C.acc + 18, C.I, tv, dw);
       for (int a = 0; a < 3; ++a) {
-        C.V[a] += (C.Fh[a] + C.Flc[a] + C.Fext[a]) / C.M;
-        C.W[a] += (C.Th[a] + C.Tlc[a]) / C.I;
+        C.V[a] += dv[a];
+        C.W[a] += dw[a];
       }
       const int L[3] = {B.nx, B.ny, B.nz};
       for (int a = 0; a < 3; ++a) {
@@ -698,7 +758,7 @@ __global__ void k_colloid(DevBox* __restrict__ boxes, int nboxes) {
         }
       }
     }
-    for (int k = 0; k < 12; ++k) C.acc[k] = 0.0;
+    for (int k = 0; k < 24; ++k) C.acc[k] = 0.0;
   }
   if (threadIdx.x == 0) {
     DevState* st = B.st;

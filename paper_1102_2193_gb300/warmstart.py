@@ -8,7 +8,7 @@
    forward/backward kernels and Adam.
 3. ``propose`` / ``compare``: the network's Q (trilinearly upsampled when the
    target box is twice the network's) replaces the helix as the start, and
-   the plain relaxation, which stays the judge and the fallback, is run from
+   the plain relaxation, which decides acceptance and is the fallback, is run from
    both starts; steps, wall time, residual and free energy are reported.
 
 The relaxation runs with the flow frozen (u = 0): the statics do not depend on

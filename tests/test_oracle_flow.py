@@ -177,10 +177,68 @@ def test_overlapping_colloids_rejected():
         o2.add_colloid((8.0, 8.0, 1.0), 3.0)
 
 
+def _drag_tensors(L, X, a0, rho0=1.0):
+    """Coefficients of the link momentum exchange linear in the rigid motion,
+    from a brute-force link enumeration: per link (fluid r, direction c into
+    the colloid), dp = -6 w rho0 c (c.(V + W x d)), d = r + c/2 - X (minimum
+    image), so F = -(zv V + zvw W), T = -(zvw^T V + zw W)."""
+    c, w = oracle.lattice()
+    nx = L[0]
+    zv, zw, zvw = np.zeros((3, 3)), np.zeros((3, 3)), np.zeros((3, 3))
+    for node, q in _brute_links(L, X, a0):
+        x, y, z = node % nx, (node // nx) % L[1], node // (nx * L[1])
+        cq = np.array(c[q], dtype=float)
+        d = np.array([x, y, z], dtype=float) + 0.5 * cq - np.array(X)
+        for k, n in enumerate(L):
+            if d[k] >= 0.5 * n:
+                d[k] -= n
+            elif d[k] < -0.5 * n:
+                d[k] += n
+        rc = np.cross(d, cq)
+        k6 = 6.0 * w[q] * rho0
+        zv += k6 * np.outer(cq, cq)
+        zw += k6 * np.outer(rc, rc)
+        zvw += k6 * np.outer(cq, rc)
+    return zv, zw, zvw
+
+
+def test_colloid_update_one_step_from_rest():
+    """Fluid at rest (df = 0, so df* = 0 on every link): the link force is purely
+    the moving-wall term, F = -(zv V + zvw W), T = -(zvw^T V + zw W), and the
+    update taking its V-V and W-W parts at the new velocity gives
+    V' = V + (M + zv)^{-1} F, W' = W + (I + zw)^{-1} T, X' = X + V'."""
+    L = (14, 13, 12)
+    X, a0 = (6.3, 5.8, 5.55), 3.4
+    o = oracle.Oracle(*L, tau=1.0, lc=False)
+    cid = o.add_colloid(X, a0, oracle.NORMAL, mobile=True)
+    V0, W0 = np.array([2e-4, -1e-4, 3e-4]), np.array([1e-4, 2e-4, -1.5e-4])
+    o.set_colloid_velocity(cid, V0, W0)
+    s0 = o.get_solid()
+    o.step(1)
+    assert (o.get_solid() == s0).all()  # no re-discretisation in this step
+    zv, zw, zvw = _drag_tensors(L, X, a0)
+    F = -(zv @ V0 + zvw @ W0)
+    T = -(zvw.T @ V0 + zw @ W0)
+    c = o.colloid(cid)
+    np.testing.assert_allclose(c["F_hyd"], F, rtol=1e-12, atol=1e-18)
+    np.testing.assert_allclose(c["T_hyd"], T, rtol=1e-12, atol=1e-18)
+    M = 4.0 / 3.0 * math.pi * a0**3
+    I = 0.4 * M * a0**2
+    V1 = V0 + np.linalg.solve(M * np.eye(3) + zv, F)
+    W1 = W0 + np.linalg.solve(I * np.eye(3) + zw, T)
+    np.testing.assert_allclose(c["V"], V1, rtol=1e-12)
+    np.testing.assert_allclose(c["W"], W1, rtol=1e-12)
+    np.testing.assert_allclose(c["X"], np.array(X) + V1, rtol=0, atol=1e-15)
+    # the implicit update damps: |V'| < |V| component-wise along V
+    assert V1 @ V0 < V0 @ V0
+
+
 def test_moving_colloid_rediscretisation_conserves_momentum():
     """Sec. 2.2 (last paragraph): a colloid moving across the lattice covers and
-    uncovers nodes; the exchanged fluid momentum goes to the colloid, so fluid
-    momentum + M V is constant (no external force)."""
+    uncovers nodes; the exchanged fluid momentum goes to the colloid.  Fluid
+    momentum + colloid impulse (link, LC and re-discretisation exchanges) is
+    constant, and every step's velocity change is the update's
+    (M + zv)^{-1} (F_hyd + F_lc) plus the re-discretisation exchange / M."""
     L = (24, 20, 18)
     o = oracle.Oracle(*L, **dict(synth.NEMATIC), threads=4)
     o.init_uniaxial((0, 0, 1), 1e-2, 3)
@@ -188,13 +246,23 @@ def test_moving_colloid_rediscretisation_conserves_momentum():
     cid = o.add_colloid((11.3, 9.6, 8.8), a0, oracle.PLANAR, 0.02, mobile=True)
     o.set_colloid_velocity(cid, (0.02, -0.01, 0.015))
     M = 4.0 / 3.0 * math.pi * a0**3
-    p0 = o.diag()["momentum"] + M * o.colloid(cid)["V"]
+    p0 = o.diag()["momentum"] + o.colloid(cid)["impulse"]
     s0 = o.get_solid()
     changes = 0
-    for _ in range(6):
-        o.step(20)
+    for k in range(40):
+        before = o.colloid(cid)
+        o.step(1)
+        after = o.colloid(cid)
         s = o.get_solid()
-        changes += int((s != s0).sum())
+        nchg = int((s != s0).sum())
+        changes += nchg
         s0 = s
-        np.testing.assert_allclose(o.diag()["momentum"] + M * o.colloid(cid)["V"], p0, atol=1e-13)
+        if k % 3 == 0 or nchg:
+            zv, _, _ = _drag_tensors(L, before["X"], a0)
+            f = after["F_hyd"] + after["F_lc"]
+            rd = after["impulse"] - before["impulse"] - f  # re-discretisation exchange
+            assert (np.abs(rd).max() > 0) == (nchg > 0) or np.abs(rd).max() < 1e-15
+            np.testing.assert_allclose(after["V"], before["V"] + np.linalg.solve(M * np.eye(3) + zv, f) + rd / M,
+                                       rtol=1e-10, atol=1e-16)
+        np.testing.assert_allclose(o.diag()["momentum"] + after["impulse"], p0, atol=1e-13)
     assert changes >= 3  # the solid set did change
