@@ -196,11 +196,19 @@ int lc_lb_diagnostics_noalloc(lc_lb* h, lc_diag* out);
 
 /* Profiling: run nsteps steps without the graph and with every kernel on
  * the handle's stream, with CUDA events around each, and return the mean
- * milliseconds per launch of: [0] fused LC stress + body force + LB
- * collide/stream, [1] Q update, [2] link momentum exchange, [3] colloid
- * update, [4] the whole step.  The state advances by nsteps.  Synchronises. */
+ * milliseconds per step of: [0] LC stress + body force + LB collide/stream
+ * (the force + LB part, in the variant the autotuner chose), [1] Q update,
+ * [2] link momentum exchange, [3] colloid update, [4] the whole step.  The
+ * _detail forms add [5] the variant (0 fused: one kernel; 1 split: stress/
+ * force kernel and LB kernel, run one after the other here; 2 stored: the
+ * stress kernel stores H and P, the LB kernel takes the face divergence of
+ * the stored P) and [6], [7] the milliseconds of its two kernels (fused:
+ * [7] = 0).  LCLB_VARIANT=fused|split|stored in the environment overrides the
+ * tuned variant.  The state advances by nsteps.  Synchronises. */
 int lc_lb_profile(lc_lb* h, int nsteps, double ms_out[5]);
 int lc_lb_batch_profile(lc_lb_batch* b, int nsteps, double ms_out[5]);
+int lc_lb_profile_detail(lc_lb* h, int nsteps, double ms_out[8]);
+int lc_lb_batch_profile_detail(lc_lb_batch* b, int nsteps, double ms_out[8]);
 int lc_lb_synchronize(lc_lb* h);
 const char* lc_lb_last_error(const lc_lb* h);
 const char* lc_lb_version(void);

@@ -19,7 +19,20 @@ LC_OK, LC_ERR_ARG, LC_ERR_CUDA, LC_ERR_OOM, LC_ERR_OVERLAP, LC_ERR_NONFINITE, LC
 LC_FP32, LC_FP64 = 0, 1
 LC_NORMAL, LC_PLANAR = 0, 1
 LC_Q, LC_U, LC_RHO, LC_F_PRE, LC_FORCE, LC_SOLID = 0, 1, 2, 3, 4, 5
-PHASES = ("flb", "lc", "links", "colloid", "step")
+PHASES = ("flb", "lc", "links", "colloid", "step")  # "flb": the force + LB part, whatever its variant
+
+VARIANTS = ("fused", "split", "stored")
+VARIANT_KERNELS = (("k_flb",), ("k_force", "k_lb"), ("k_stress", "k_lbp"))
+
+
+def _profile_dict(ms) -> dict:
+    out = dict(zip(PHASES, ms[:5].tolist()))
+    v = int(round(ms[5]))
+    out["variant"] = VARIANTS[v]
+    out["kernels"] = dict(zip(VARIANT_KERNELS[v], ms[6:8].tolist()))
+    return out
+
+
 _NCOMP = {LC_Q: 5, LC_U: 3, LC_RHO: 1, LC_F_PRE: 19, LC_FORCE: 3, LC_SOLID: 1}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -119,6 +132,8 @@ def lib(use_torch_allocator: bool = True):
         L.lc_lb_diagnostics_noalloc.argtypes = [vp, C.POINTER(lc_diag)]
         L.lc_lb_profile.argtypes = [vp, C.c_int, dp]
         L.lc_lb_batch_profile.argtypes = [vp, C.c_int, dp]
+        L.lc_lb_profile_detail.argtypes = [vp, C.c_int, dp]
+        L.lc_lb_batch_profile_detail.argtypes = [vp, C.c_int, dp]
         L.lc_lb_synchronize.argtypes = [vp]
         L.lc_lb_last_error.argtypes = [vp]
         L.lc_lb_last_error.restype = C.c_char_p
@@ -325,10 +340,11 @@ class Solver:
         self._check(self.L.lc_lb_synchronize(self.h))
 
     def profile(self, n=10) -> dict:
-        """Mean ms per launch of each phase over n non-graph steps (advances the state)."""
-        ms = np.empty(5)
-        self._check(self.L.lc_lb_profile(self.h, int(n), _dp(ms)))
-        return dict(zip(PHASES, ms.tolist()))
+        """Mean ms per step of each phase over n non-graph steps (advances the
+        state), the step variant and its force + LB kernels."""
+        ms = np.empty(8)
+        self._check(self.L.lc_lb_profile_detail(self.h, int(n), _dp(ms)))
+        return _profile_dict(ms)
 
     def diag(self) -> dict:
         d = lc_diag()
@@ -384,9 +400,9 @@ class Batch:
         return s.value, r
 
     def profile(self, n=10) -> dict:
-        ms = np.empty(5)
-        self._check(self.L.lc_lb_batch_profile(self.h, int(n), _dp(ms)))
-        return dict(zip(PHASES, ms.tolist()))
+        ms = np.empty(8)
+        self._check(self.L.lc_lb_batch_profile_detail(self.h, int(n), _dp(ms)))
+        return _profile_dict(ms)
 
     def close(self):
         if getattr(self, "h", None):

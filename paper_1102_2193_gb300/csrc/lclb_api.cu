@@ -38,6 +38,10 @@ struct TileCfg {
   int ty = 4, zc = 16, persistent = 0;
 };
 
+constexpr int NPHASE = 6;
+// partial-sum doubles per tile of each phase
+constexpr int PART_WIDTH[NPHASE] = {1, 4, 2, 1, 1, 1};
+
 struct Phase {
   TileCfg cfg;
   int4* d_tiles = nullptr;
@@ -101,12 +105,15 @@ struct Group {
   Mem mem;
   std::vector<lc_lb*> boxes;
   DevBox* d_boxes = nullptr;
-  Phase ph[4];  // 0 force (diagnostics/export), 1 lb (unused by the step), 2 lc, 3 fused force+lb (step)
+  // 0 force (diagnostics/export; split variant), 1 lb (split variant), 2 lc,
+  // 3 fused force+lb (fused variant), 4 stress, 5 lb from stored stress (stored variant)
+  Phase ph[NPHASE];
   cudaStream_t side = nullptr;   // second stream: link momentum exchange runs beside the Q update
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // Step variant: 0 = fused stress/force/LB kernel; 1 = split: the stress/
   // force kernel and the LB kernel run concurrently in z slabs on two streams
-  // (LB slab s waits for force slab s only).
+  // (LB slab s waits for force slab s only); 2 = stored: H and P stored once
+  // per node, then the LB kernel takes the face divergence of the stored P.
   int variant = 0;
   int slab = 0;                              // slab thickness in z (0: whole box)
   cudaStream_t side2 = nullptr;
@@ -182,8 +189,7 @@ int build_phase(Group* g, int k) {
   P.d_tiles = (int4*)galloc(g, sizeof(int4) * tl.size());
   if (!P.d_tiles) return fail(&g->err, LC_ERR_OOM, "tile list allocation failed");
   CK(cudaMemcpyAsync(P.d_tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice, g->stream), &g->err);
-  const int width = k == 0 ? 1 : (k == 1 ? 4 : (k == 2 ? 2 : 1));
-  const size_t need = (size_t)width * tl.size();
+  const size_t need = (size_t)PART_WIDTH[k] * tl.size();
   if (need > P.part_cap) {
     if (P.d_part) g->mem.put(P.d_part, g->al);
     P.d_part = (double*)galloc(g, sizeof(double) * need);
@@ -312,16 +318,20 @@ int make_box(Group* g, const lc_grid* G, const lc_params* p, lc_lb* h) {
   B.u = galloc(g, 3 * N * ts);
   B.F = galloc(g, 3 * N * ts);
   B.H = galloc(g, 5 * N * ts);
+  B.P = galloc(g, 9 * N * ts);
   B.mask = (uint8_t*)galloc(g, N);
   B.col = (DevColloid*)galloc(g, sizeof(DevColloid) * MAXCOL);
   B.st = (DevState*)galloc(g, sizeof(DevState));
   B.nlinks = (int*)galloc(g, sizeof(int));
-  if (!B.f[0] || !B.f[1] || !B.Q[0] || !B.Q[1] || !B.u || !B.F || !B.H || !B.mask || !B.col || !B.st || !B.nlinks)
+  if (!B.f[0] || !B.f[1] || !B.Q[0] || !B.Q[1] || !B.u || !B.F || !B.H || !B.P || !B.mask || !B.col || !B.st ||
+      !B.nlinks)
     return fail(&h->err, LC_ERR_OOM, "device allocation failed for a %dx%dx%d box", G->nx, G->ny, G->nz);
   cudaStream_t s = g->stream;
   for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(B.f[k], 0, NQ * N * ts, s), &h->err);
   CK(cudaMemsetAsync(B.u, 0, 3 * N * ts, s), &h->err);
   CK(cudaMemsetAsync(B.F, 0, 3 * N * ts, s), &h->err);
+  CK(cudaMemsetAsync(B.H, 0, 5 * N * ts, s), &h->err);
+  CK(cudaMemsetAsync(B.P, 0, 9 * N * ts, s), &h->err);
   CK(cudaMemsetAsync(B.mask, 0, N, s), &h->err);
   CK(cudaMemsetAsync(B.col, 0, sizeof(DevColloid) * MAXCOL, s), &h->err);
   CK(cudaMemsetAsync(B.nlinks, 0, sizeof(int), s), &h->err);
@@ -417,20 +427,31 @@ TuneKey tune_key(Group* g) {
 }
 
 // Optional file cache (LCLB_TUNE_CACHE): one line per entry,
-// "signature precision ty zc persistent x3".
+// "signature precision" and NCFG triples "ty zc persistent" (fused, lc,
+// force, lb, (variant, slab, 0), stress, lb-from-stress); lines of another
+// length are skipped.
+constexpr int NCFG = 7;
 void tune_file_load() {
   const char* path = getenv("LCLB_TUNE_CACHE");
   if (!path) return;
   FILE* f = fopen(path, "r");
   if (!f) return;
-  long long sig;
-  int prec, v[15];
-  while (fscanf(f, "%lld %d", &sig, &prec) == 2) {
-    bool ok = true;
-    for (int k = 0; k < 15 && ok; ++k) ok = fscanf(f, "%d", &v[k]) == 1;
-    if (!ok) break;
-    std::vector<TileCfg> c(5);
-    for (int k = 0; k < 5; ++k) c[k] = TileCfg{v[3 * k], v[3 * k + 1], v[3 * k + 2]};
+  char line[1024];
+  while (fgets(line, sizeof(line), f)) {
+    long long sig;
+    int prec, v[3 * NCFG], used = 0, n = 0;
+    if (sscanf(line, "%lld %d%n", &sig, &prec, &used) != 2) continue;
+    const char* q = line + used;
+    while (n < 3 * NCFG) {
+      int adv = 0;
+      if (sscanf(q, "%d%n", &v[n], &adv) != 1) break;
+      q += adv;
+      ++n;
+    }
+    int extra = 0;
+    if (n != 3 * NCFG || sscanf(q, "%d", &extra) == 1) continue;
+    std::vector<TileCfg> c(NCFG);
+    for (int k = 0; k < NCFG; ++k) c[k] = TileCfg{v[3 * k], v[3 * k + 1], v[3 * k + 2]};
     g_tune_cache[TuneKey(sig, prec)] = c;
   }
   fclose(f);
@@ -442,18 +463,19 @@ void tune_file_store(const TuneKey& key, const std::vector<TileCfg>& c) {
   FILE* f = fopen(path, "a");
   if (!f) return;
   fprintf(f, "%lld %d", std::get<0>(key), std::get<1>(key));
-  for (int k = 0; k < 5; ++k) fprintf(f, " %d %d %d", c[k].ty, c[k].zc, c[k].persistent);
+  for (int k = 0; k < NCFG; ++k) fprintf(f, " %d %d %d", c[k].ty, c[k].zc, c[k].persistent);
   fprintf(f, "\n");
   fclose(f);
 }
 
 cudaError_t launch_phase(Group* g, int k, int mode, int box = -1) {
   Launch L = phase_launch(g, k, box);
-  const int width = k == 0 ? 1 : (k == 1 ? 4 : (k == 2 ? 2 : 1));
-  double* part = g->ph[k].d_part + (box < 0 ? 0 : (size_t)g->ph[k].start[box] * width);
+  double* part = g->ph[k].d_part + (box < 0 ? 0 : (size_t)g->ph[k].start[box] * PART_WIDTH[k]);
   if (k == 0) return launch_force(g->prec, L, mode, part);
   if (k == 1) return launch_lb(g->prec, L, mode, part);
   if (k == 2) return launch_lc(g->prec, L, mode, part);
+  if (k == 4) return launch_stress(g->prec, L, mode, part);
+  if (k == 5) return launch_lbp(g->prec, L, mode, part);
   return launch_flb(g->prec, L, mode, part);
 }
 
@@ -480,12 +502,40 @@ int tune_phase_fn(Group* g, void* arg) {
   return LC_OK;
 }
 int tune_split_fn(Group* g, void*) { return enqueue_split(g, 0); }
+int tune_stored_fn(Group* g, void*) {
+  CK(launch_phase(g, 4, 0), &g->err);
+  CK(launch_phase(g, 5, 0), &g->err);
+  return LC_OK;
+}
 
 // Time every candidate tile shape of each phase kernel on the group's own
 // state (the phase kernels are idempotent between parity flips), then the
 // slab thickness of the split variant, then fused against split, and keep
 // the fastest.
+int autotune_group_inner(Group* g, std::string* desc);
+
+// The LB kernels read f in place while the populations are pre-collision
+// (just after initialisation or set_fields) and pull from the neighbours in
+// every later step; tune on the pull path, then put each box's state back.
 int autotune_group(Group* g, std::string* desc) {
+  std::vector<DevState> saved(g->boxes.size());
+  for (size_t b = 0; b < g->boxes.size(); ++b) {
+    lc_lb* h = g->boxes[b];
+    CK(cudaMemcpyAsync(&saved[b], h->hb.st, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream), &g->err);
+  }
+  CK(cudaStreamSynchronize(g->stream), &g->err);
+  for (size_t b = 0; b < g->boxes.size(); ++b) {
+    if (!saved[b].pre_valid) continue;
+    CK(cudaMemsetAsync(&g->boxes[b]->hb.st->pre_valid, 0, sizeof(int), g->stream), &g->err);
+  }
+  const int rc = autotune_group_inner(g, desc);
+  for (size_t b = 0; b < g->boxes.size(); ++b)
+    CK(cudaMemcpyAsync(g->boxes[b]->hb.st, &saved[b], sizeof(DevState), cudaMemcpyHostToDevice, g->stream), &g->err);
+  CK(cudaStreamSynchronize(g->stream), &g->err);
+  return rc;
+}
+
+int autotune_group_inner(Group* g, std::string* desc) {
   const int pers[3] = {0, 2, 4};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), &g->err);
@@ -493,11 +543,14 @@ int autotune_group(Group* g, std::string* desc) {
   char buf[256];
   std::string out;
   int rc = LC_OK;
-  float best_phase[4] = {1e30f, 1e30f, 1e30f, 1e30f};
-  for (int k : {3, 2, 0, 1}) {
+  float best_phase[NPHASE] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
+  const char* venv = getenv("LCLB_TUNE_VERBOSE");
+  const bool verbose = venv && venv[0] == '1';
+  for (int k : {3, 2, 0, 1, 4, 5}) {
     TileCfg best = g->ph[k].cfg;
     const std::vector<int> tys = k == 3 ? std::vector<int>{4, 6, 8} : std::vector<int>{2, 4, 8};
-    const std::vector<int> zcs = k == 1 ? std::vector<int>{1, 2, 4, 8, 16} : std::vector<int>{2, 4, 8, 16, 32, 64};
+    const std::vector<int> zcs =
+        (k == 1 || k == 5) ? std::vector<int>{1, 2, 4, 8, 16} : std::vector<int>{2, 4, 8, 16, 32, 64};
     for (int ty : tys)
       for (int zc : zcs)
         for (int pp : pers) {
@@ -506,6 +559,7 @@ int autotune_group(Group* g, std::string* desc) {
           int kk = k;
           const float ms = time_ms(g, e0, e1, 3, tune_phase_fn, &kk, &rc);
           if (rc) return rc;
+          if (verbose) fprintf(stderr, "lclb tune phase %d ty=%d zc=%d pers=%d %.1f us\n", k, ty, zc, pp, 1000.f * ms);
           if (ms < best_phase[k]) {
             best_phase[k] = ms;
             best = g->ph[k].cfg;
@@ -514,7 +568,8 @@ int autotune_group(Group* g, std::string* desc) {
     g->ph[k].cfg = best;
     if ((rc = build_phase(g, k))) return rc;
     snprintf(buf, sizeof(buf), "%s:ty=%d,zc=%d,pers=%d(%.1fus) ",
-             k == 3 ? "flb" : (k == 2 ? "lc" : (k == 0 ? "force" : "lb")), best.ty, best.zc, best.persistent,
+             k == 3 ? "flb" : (k == 2 ? "lc" : (k == 0 ? "force" : (k == 1 ? "lb" : (k == 4 ? "stress" : "lbp")))),
+             best.ty, best.zc, best.persistent,
              1000.f * best_phase[k]);
     out += buf;
   }
@@ -531,6 +586,7 @@ int autotune_group(Group* g, std::string* desc) {
     if ((rc = build_chunks_slab(g))) return rc;
     const float ms = time_ms(g, e0, e1, 3, tune_split_fn, nullptr, &rc);
     if (rc) return rc;
+    if (verbose) fprintf(stderr, "lclb tune split slab=%d %.1f us\n", g->slab, 1000.f * ms);
     if (ms < best_split) {
       best_split = ms;
       best_slab = g->slab;
@@ -538,16 +594,25 @@ int autotune_group(Group* g, std::string* desc) {
   }
   g->slab = best_slab;
   if ((rc = build_chunks_slab(g))) return rc;
-  g->variant = best_split < best_phase[3] ? 1 : 0;
-  snprintf(buf, sizeof(buf), "split(slab=%d,%.1fus) -> %s", best_slab, 1000.f * best_split,
-           g->variant ? "split" : "fused");
+  const float stored = time_ms(g, e0, e1, 3, tune_stored_fn, nullptr, &rc);
+  if (rc) return rc;
+  if (verbose) fprintf(stderr, "lclb tune stored %.1f us\n", 1000.f * stored);
+  g->variant = 0;
+  float best_var = best_phase[3];
+  if (best_split < best_var) {
+    g->variant = 1;
+    best_var = best_split;
+  }
+  if (stored < best_var) g->variant = 2;
+  snprintf(buf, sizeof(buf), "split(slab=%d,%.1fus) stored(%.1fus) -> %s", best_slab, 1000.f * best_split,
+           1000.f * stored, g->variant == 0 ? "fused" : (g->variant == 1 ? "split" : "stored"));
   out += buf;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     g_tune_cache[tune_key(g)] = {g->ph[3].cfg, g->ph[2].cfg, g->ph[0].cfg, g->ph[1].cfg,
-                                 TileCfg{g->variant, g->slab, 0}};
+                                 TileCfg{g->variant, g->slab, 0}, g->ph[4].cfg, g->ph[5].cfg};
     tune_file_store(tune_key(g), g_tune_cache[tune_key(g)]);
   }
   g->tuned = true;
@@ -556,8 +621,22 @@ int autotune_group(Group* g, std::string* desc) {
   return LC_OK;
 }
 
+// LCLB_VARIANT=fused|split|stored forces the force + LB variant of the step
+// (the tile shapes stay tuned); used to run every variant through the same tests.
+int apply_variant_override(Group* g) {
+  const char* v = getenv("LCLB_VARIANT");
+  if (!v || !v[0]) return LC_OK;
+  const int want = !strcmp(v, "fused") ? 0 : (!strcmp(v, "split") ? 1 : (!strcmp(v, "stored") ? 2 : -1));
+  if (want < 0) return fail(&g->err, LC_ERR_ARG, "LCLB_VARIANT must be fused, split or stored (got %s)", v);
+  if (want != g->variant) {
+    g->variant = want;
+    g->dirty = true;
+  }
+  return LC_OK;
+}
+
 int maybe_tune(Group* g) {
-  if (g->tuned) return LC_OK;
+  if (g->tuned) return apply_variant_override(g);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     static bool loaded = false;
@@ -573,20 +652,25 @@ int maybe_tune(Group* g) {
       g->ph[1].cfg = it->second[3];
       g->variant = it->second[4].ty;
       g->slab = it->second[4].zc;
+      g->ph[4].cfg = it->second[5];
+      g->ph[5].cfg = it->second[6];
       g->tuned = true;
     }
   }
+  int rc = LC_OK;
   if (g->tuned) {
-    for (int k = 0; k < 4; ++k)
-      if (int rc = build_phase(g, k)) return rc;
-    return build_chunks_slab(g);
+    for (int k = 0; k < NPHASE && !rc; ++k) rc = build_phase(g, k);
+    if (!rc) rc = build_chunks_slab(g);
+  } else {
+    const char* env = getenv("LCLB_AUTOTUNE");
+    if (env && env[0] == '0') {
+      g->tuned = true;
+      rc = build_chunks_slab(g);
+    } else {
+      rc = autotune_group(g, nullptr);
+    }
   }
-  const char* env = getenv("LCLB_AUTOTUNE");
-  if (env && env[0] == '0') {
-    g->tuned = true;
-    return build_chunks_slab(g);
-  }
-  return autotune_group(g, nullptr);
+  return rc ? rc : apply_variant_override(g);
 }
 
 // ---- one step -----------------------------------------------------------------
@@ -660,13 +744,19 @@ int enqueue_split(Group* g, int force_mode) {
 // update on the main stream and the link momentum exchange on the side
 // stream (both read only what the fused kernel wrote), joined before the
 // colloid update.
-int enqueue_step(Group* g) {
-  if (g->variant == 1) {
-    int rc = enqueue_split(g, FORCE_ACC);
-    if (rc) return rc;
-  } else {
-    CK(launch_phase(g, 3, FORCE_ACC), &g->err);
+int enqueue_force_lb(Group* g) {
+  if (g->variant == 1) return enqueue_split(g, FORCE_ACC);
+  if (g->variant == 2) {
+    CK(launch_phase(g, 4, FORCE_ACC), &g->err);
+    CK(launch_phase(g, 5, 0), &g->err);
+    return LC_OK;
   }
+  CK(launch_phase(g, 3, FORCE_ACC), &g->err);
+  return LC_OK;
+}
+
+int enqueue_step(Group* g) {
+  if (int rc = enqueue_force_lb(g)) return rc;
   if (g->nchunks > 0) {
     CK(cudaEventRecord(g->ev_fork, g->stream), &g->err);
     CK(cudaStreamWaitEvent(g->side, g->ev_fork, 0), &g->err);
@@ -741,20 +831,25 @@ int capture(Group* g) {
 }
 
 // Non-graph steps with events around each phase; mean ms per launch.
+// Non-graph steps with every kernel on the main stream and events around
+// each part; ms[0..4] = mean ms per step of the force + LB part, the Q
+// update, the link exchange, the colloid update and the whole step; ms[5] =
+// the variant, ms[6], ms[7] = the two kernels of the force + LB part (fused:
+// k_flb and 0; split: k_force and k_lb, run one after the other here;
+// stored: k_stress and k_lbp).
 int group_profile(Group* g, int n, double* ms) {
   int rc = maybe_tune(g);
   if (rc) return rc;
   cudaEvent_t ev[6];
   for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&ev[k]), &g->err);
-  double acc[5] = {0, 0, 0, 0, 0};
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const int k1 = g->variant == 0 ? 3 : (g->variant == 1 ? 0 : 4);
+  const int k2 = g->variant == 0 ? -1 : (g->variant == 1 ? 1 : 5);
   for (int s = 0; s < n; ++s) {
     CK(cudaEventRecord(ev[0], g->stream), &g->err);
-    if (g->variant == 1) {
-      int rc2 = enqueue_split(g, FORCE_ACC);
-      if (rc2) return rc2;
-    } else {
-      CK(launch_phase(g, 3, FORCE_ACC), &g->err);
-    }
+    CK(launch_phase(g, k1, FORCE_ACC), &g->err);
+    CK(cudaEventRecord(ev[5], g->stream), &g->err);
+    if (k2 >= 0) CK(launch_phase(g, k2, 0), &g->err);
     CK(cudaEventRecord(ev[1], g->stream), &g->err);
     CK(launch_phase(g, 2, LC_RESID), &g->err);
     CK(cudaEventRecord(ev[2], g->stream), &g->err);
@@ -774,9 +869,14 @@ int group_profile(Group* g, int n, double* ms) {
     float t = 0.f;
     cudaEventElapsedTime(&t, ev[0], ev[4]);
     acc[4] += t;
+    cudaEventElapsedTime(&t, ev[0], ev[5]);
+    acc[5] += t;
   }
   for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
-  for (int k = 0; k < 5; ++k) ms[k] = n > 0 ? acc[k] / n : 0.0;
+  for (int k = 0; k < 5; ++k) ms[k] = acc[k] / n;
+  ms[5] = g->variant;
+  ms[6] = acc[5] / n;
+  ms[7] = k2 >= 0 ? (acc[0] - acc[5]) / n : 0.0;
   return LC_OK;
 }
 
@@ -907,7 +1007,7 @@ int lc_lb_create(const lc_grid* grid, const lc_params* params, void* stream, lc_
   g->boxes.push_back(h);
   rc = make_box(g, grid, params, h);
   if (!rc) rc = rebuild_geometry(h);
-  for (int k = 0; k < 4 && !rc; ++k) rc = build_phase(g, k);
+  for (int k = 0; k < NPHASE && !rc; ++k) rc = build_phase(g, k);
   if (!rc) rc = build_chunks(g);
   if (rc) {
     g_err = h->err.empty() ? g->err : h->err;
@@ -1209,7 +1309,7 @@ int lc_lb_diagnostics(lc_lb* h, lc_diag* out) {
   return LC_OK;
 }
 
-int lc_lb_profile(lc_lb* h, int nsteps, double ms_out[5]) {
+int lc_lb_profile_detail(lc_lb* h, int nsteps, double ms_out[8]) {
   if (int rc = h_check(h)) return rc;
   if (!h->owns_group) return fail(&h->err, LC_ERR_STATE, "box of a batch: profile the batch");
   if (nsteps < 1 || !ms_out) return fail(&h->err, LC_ERR_ARG, "bad profile arguments");
@@ -1218,10 +1318,26 @@ int lc_lb_profile(lc_lb* h, int nsteps, double ms_out[5]) {
   return rc;
 }
 
-int lc_lb_batch_profile(lc_lb_batch* b, int nsteps, double ms_out[5]) {
+int lc_lb_profile(lc_lb* h, int nsteps, double ms_out[5]) {
+  double ms[8];
+  int rc = lc_lb_profile_detail(h, nsteps, ms_out ? ms : nullptr);
+  if (!rc)
+    for (int k = 0; k < 5; ++k) ms_out[k] = ms[k];
+  return rc;
+}
+
+int lc_lb_batch_profile_detail(lc_lb_batch* b, int nsteps, double ms_out[8]) {
   if (!b || nsteps < 1 || !ms_out) return fail(b ? &b->err : nullptr, LC_ERR_ARG, "bad profile arguments");
   int rc = group_profile(b->g, nsteps, ms_out);
   if (rc) b->err = b->g->err;
+  return rc;
+}
+
+int lc_lb_batch_profile(lc_lb_batch* b, int nsteps, double ms_out[5]) {
+  double ms[8];
+  int rc = lc_lb_batch_profile_detail(b, nsteps, ms_out ? ms : nullptr);
+  if (!rc)
+    for (int k = 0; k < 5; ++k) ms_out[k] = ms[k];
   return rc;
 }
 
@@ -1316,7 +1432,7 @@ int lc_lb_batch_create(int n, const lc_grid* grids, const lc_params* params, voi
     if (!rc) rc = rebuild_geometry(h);
     if (rc) g_err = h->err;
   }
-  for (int k = 0; k < 4 && !rc; ++k) rc = build_phase(g, k);
+  for (int k = 0; k < NPHASE && !rc; ++k) rc = build_phase(g, k);
   if (!rc) rc = build_chunks(g);
   if (rc) {
     free_group(g);

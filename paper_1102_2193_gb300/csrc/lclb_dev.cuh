@@ -84,6 +84,7 @@ struct DevBox {
   void* u;
   void* F;
   void* H;              // molecular field of the current Q at fluid nodes (5 comps), written by the stress kernels
+  void* P;              // chemical stress at fluid nodes (9 comps, row-major P_ab), stored-stress variant only
   uint8_t* mask;
   DevColloid* col;
   DevState* st;
@@ -529,16 +530,19 @@ __device__ __forceinline__ void lc_node(const PhysT<T>& P, const T qi[5], const 
     }
   h[0] = H[0][0]; h[1] = H[0][1]; h[2] = H[0][2]; h[3] = H[1][1]; h[4] = H[1][2];
   if (!NEED_P) return;
-  T E[3][3];
+  // E_ab = K d_aQ : d_bQ; both factors are symmetric and traceless, so the
+  // double contraction over the 5 stored components is
+  // A_xx B_xx + A_yy B_yy + A_zz B_zz + 2 (A_xy B_xy + A_xz B_xz + A_yz B_yz)
+  // with A_zz = -(A_xx + A_yy)
+  T E[3][3], tz[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) tz[a] = dq[a][0] + dq[a][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = a; b < 3; ++b) {
-      T e = T(0);
-#pragma unroll
-      for (int gg = 0; gg < 3; ++gg)
-#pragma unroll
-        for (int n = 0; n < 3; ++n) e += D[a][gg][n] * D[b][gg][n];
+      const T e = dq[a][0] * dq[b][0] + dq[a][3] * dq[b][3] + tz[a] * tz[b] +
+                  T(2) * (dq[a][1] * dq[b][1] + dq[a][2] * dq[b][2] + dq[a][4] * dq[b][4]);
       E[a][b] = K * e;
       E[b][a] = K * e;
     }

@@ -31,6 +31,8 @@ cudaError_t launch_force(int prec, const Launch& L, int mode, double* part);
 cudaError_t launch_lb(int prec, const Launch& L, int mode, double* part);
 cudaError_t launch_flb(int prec, const Launch& L, int mode, double* part);  // ty in {4, 6, 8}
 cudaError_t launch_lc(int prec, const Launch& L, int mode, double* part);
+cudaError_t launch_stress(int prec, const Launch& L, int mode, double* part);  // H, P stored; colloid LC force
+cudaError_t launch_lbp(int prec, const Launch& L, int mode, double* part);     // LB with the force from stored P
 cudaError_t launch_links(int prec, const DevBox* boxes, const int2* chunks, int nchunks, int grid, cudaStream_t s);
 cudaError_t launch_colloid(DevBox* boxes, int nboxes, cudaStream_t s);
 // Re-discretisation after the colloid update; mob lists (box, colloid) of mobile colloids.

@@ -112,6 +112,33 @@ __device__ __forceinline__ uint8_t stress_at(const DevBox& B, const PhysT<T>& PP
   return 0;
 }
 
+// Colloid c takes -sgn P_{.,ax}(i) through the face of fluid node (x, y, kc)
+// on its side (Eq. 8), with the moment about its centre; summed per thread
+// into my_acc (F, T) for colloid my_c.
+template <typename T>
+__device__ __forceinline__ void colloid_face(const DevBox& B, int c, int ax, T sgn, const T pcv[3], int x, int y,
+                                             int kc, int& my_c, double my_acc[6]) {
+  const DevColloid& C = B.col[c];
+  const double ff[3] = {-(double)sgn * (double)pcv[0], -(double)sgn * (double)pcv[1], -(double)sgn * (double)pcv[2]};
+  double r[3];
+  const double hx2 = 0.5 * (double)(ax == 0 ? sgn : 0), hy2 = 0.5 * (double)(ax == 1 ? sgn : 0),
+               hz2 = 0.5 * (double)(ax == 2 ? sgn : 0);
+  disp(B, (double)x + hx2, (double)y + hy2, (double)kc + hz2, C.X, r);
+  const double tq[3] = {r[1] * ff[2] - r[2] * ff[1], r[2] * ff[0] - r[0] * ff[2], r[0] * ff[1] - r[1] * ff[0]};
+  if (my_c >= 0 && my_c != c) {  // a second colloid at this node: flush the first directly
+    for (int a = 0; a < 6; ++a) {
+      atomicAdd(&B.col[my_c].acc[6 + a], my_acc[a]);
+      my_acc[a] = 0.0;
+    }
+  }
+  my_c = c;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    my_acc[a] += ff[a];
+    my_acc[3 + a] += tq[a];
+  }
+}
+
 // Body force at interior fluid position pc (plane slot s0; the planes below
 // and above in slots sm, sp): F_a = sum_d [P_ad(face +d) - P_ad(face -d)],
 // a fluid-fluid face carrying (P_i + P_j)/2 and a solid or wall face P_i.
@@ -136,28 +163,7 @@ __device__ __forceinline__ void face_force(const DevBox& B, const T* sP, const u
       const T face = (fj == 0) ? T(0.5) * (pcv[a] + sP[(nslot[d] * 9 + 3 * a + ax) * HP + npos[d]]) : pcv[a];
       Fv[a] += sgn * face;
     }
-    if (acc && fj != 0 && fj != WALLFLAG) {
-      const int c = fj - 1;
-      const DevColloid& C = B.col[c];
-      const double ff[3] = {-(double)sgn * (double)pcv[0], -(double)sgn * (double)pcv[1], -(double)sgn * (double)pcv[2]};
-      double r[3];
-      const double hx2 = 0.5 * (double)(ax == 0 ? sgn : 0), hy2 = 0.5 * (double)(ax == 1 ? sgn : 0),
-                   hz2 = 0.5 * (double)(ax == 2 ? sgn : 0);
-      disp(B, (double)x + hx2, (double)y + hy2, (double)kc + hz2, C.X, r);
-      const double tq[3] = {r[1] * ff[2] - r[2] * ff[1], r[2] * ff[0] - r[0] * ff[2], r[0] * ff[1] - r[1] * ff[0]};
-      if (my_c >= 0 && my_c != c) {  // a second colloid at this node: flush the first directly
-        for (int a = 0; a < 6; ++a) {
-          atomicAdd(&B.col[my_c].acc[6 + a], my_acc[a]);
-          my_acc[a] = 0.0;
-        }
-      }
-      my_c = c;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        my_acc[a] += ff[a];
-        my_acc[3 + a] += tq[a];
-      }
-    }
+    if (acc && fj != 0 && fj != WALLFLAG) colloid_face(B, fj - 1, ax, sgn, pcv, x, y, kc, my_c, my_acc);
   }
 }
 
@@ -375,6 +381,139 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * 
         Fx += Fb[i];
         Fy += Fb[(size_t)N + i];
         Fz += Fb[(size_t)2 * N + i];
+      }
+      collide_store(PP, fout, ub, N, i, df, Fx, Fy, Fz);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stored-stress variant: k_stress stores H and P once per fluid node, k_lbp
+// takes the body force from the stored P
+// ---------------------------------------------------------------------------
+template <typename T, int TY>
+__global__ void __launch_bounds__(TX * TY) k_stress(const DevBox* __restrict__ boxes, const int4* __restrict__ tiles,
+                                                    int ntiles, int zc, int mode, double* __restrict__ part) {
+  __shared__ DevBox B;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int4 td = tiles[t];
+    load_box(B, boxes, td.x);
+    if (!B.p.lc_on) continue;
+    const PhysT<T>& PP = phys<T>(B);
+    const T* __restrict__ Q = static_cast<const T*>(B.Q[B.st->qpar]);
+    T* __restrict__ Hb = static_cast<T*>(B.H);
+    T* __restrict__ Pb = static_cast<T*>(B.P);
+    const int nx = B.nx, ny = B.ny, N = B.N;
+    const int x = td.y + threadIdx.x, y = td.z + threadIdx.y;
+    const int zend = min(td.w + zc, B.nz);
+    int my_c = -1;
+    double my_acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (x < nx && y < ny) {
+      for (int z = td.w; z < zend; ++z) {
+        const int i = x + nx * (y + ny * z);
+        const uint8_t m = B.mask[i];
+        if (m & IDMASK) continue;
+        T qi[5], qn[6][5], h[5], p[9], fp;
+        gather_q(B, Q, x, y, z, i, m, qi, qn, nullptr);
+        lc_node<T, true>(PP, qi, qn, h, p, &fp);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) Hb[(size_t)c * N + i] = h[c];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) Pb[(size_t)c * N + i] = p[c];
+        if ((mode & FORCE_ACC) && (m & NEAR)) {
+          int nb[6], zz[2];
+          face_neighbours(B, x, y, z, nb, zz);
+#pragma unroll
+          for (int d = 0; d < 6; ++d) {
+            const int j = nb[d];
+            if (j < 0) continue;
+            const uint8_t fj = B.mask[j] & IDMASK;
+            if (fj == 0) continue;
+            const int ax = d >> 1;
+            const T sgn = (d & 1) ? T(-1) : T(1);
+            const T pcv[3] = {p[ax], p[3 + ax], p[6 + ax]};
+            colloid_face(B, fj - 1, ax, sgn, pcv, x, y, z, my_c, my_acc);
+          }
+        }
+      }
+    }
+    if (mode & FORCE_ACC) warp_flush_colloid(B.col, my_c, my_acc, 6);
+  }
+}
+
+// Body force at fluid node i from the stored stress: the face divergence of
+// k_flb, sum over the six faces of +-(face value), the face value the mean of
+// the two nodes' P or, across a solid or wall face, P(i).  With six fluid
+// neighbours the P(i) halves cancel.
+template <typename T>
+__device__ __forceinline__ void stored_force(const DevBox& B, const T* __restrict__ Pb, int x, int y, int z, int i,
+                                             uint8_t m, T F[3]) {
+  const size_t N = (size_t)B.N;
+  int nb[6], zz[2];
+  face_neighbours(B, x, y, z, nb, zz);
+  if (!(m & NEAR)) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T* Pa = Pb + (size_t)(3 * a) * N;
+      F[a] = T(0.5) * ((ldg(Pa + nb[0]) - ldg(Pa + nb[1])) + (ldg(Pa + N + nb[2]) - ldg(Pa + N + nb[3])) +
+                       (ldg(Pa + 2 * N + nb[4]) - ldg(Pa + 2 * N + nb[5])));
+    }
+    return;
+  }
+  F[0] = F[1] = F[2] = T(0);
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const int j = nb[d];
+    const bool fluid = j >= 0 && (B.mask[j] & IDMASK) == 0;
+    const int ax = d >> 1;
+    const T sgn = (d & 1) ? T(-1) : T(1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T* Pc = Pb + (size_t)(3 * a + ax) * N;
+      const T pc = ldg(Pc + i);
+      const T face = fluid ? T(0.5) * (pc + ldg(Pc + j)) : pc;
+      F[a] += sgn * face;
+    }
+  }
+}
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * TY)) k_lbp(
+    const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
+    double* __restrict__ part) {
+  __shared__ DevBox B;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int4 td = tiles[t];
+    load_box(B, boxes, td.x);
+    if (!B.p.flow_on) continue;
+    const PhysT<T>& PP = phys<T>(B);
+    const int fpar = B.st->fpar;
+    const bool pre = B.st->pre_valid != 0;
+    const T* __restrict__ fin = static_cast<const T*>(B.f[fpar]);
+    T* __restrict__ fout = static_cast<T*>(B.f[fpar ^ 1]);
+    const T* __restrict__ Pb = static_cast<const T*>(B.P);
+    T* __restrict__ ub = static_cast<T*>(B.u);
+    const int nx = B.nx, ny = B.ny, N = B.N;
+    const int x = td.y + threadIdx.x, y = td.z + threadIdx.y;
+    const int zend = min(td.w + zc, B.nz);
+    if (x >= nx || y >= ny) continue;
+    const bool lc = B.p.lc_on != 0;
+    for (int z = td.w; z < zend; ++z) {
+      const int i = x + nx * (y + ny * z);
+      const uint8_t m = B.mask[i];
+      if (m & IDMASK) {
+        solid_velocity(B, ub, x, y, z, i, m);
+        continue;
+      }
+      T df[NQ];
+      pull(B, fin, x, y, z, i, m, pre, df);
+      T Fx = PP.g[0], Fy = PP.g[1], Fz = PP.g[2];
+      if (lc) {
+        T Fv[3];
+        stored_force(B, Pb, x, y, z, i, m, Fv);
+        Fx += Fv[0];
+        Fy += Fv[1];
+        Fz += Fv[2];
       }
       collide_store(PP, fout, ub, N, i, df, Fx, Fy, Fz);
     }
@@ -1406,6 +1545,18 @@ static cudaError_t launch_flb_t(const Launch& L, int mode, double* part) {
 }
 
 template <typename T, int TY>
+static cudaError_t launch_stress_t(const Launch& L, int mode, double* part) {
+  k_stress<T, TY><<<L.grid, dim3(TX, TY), 0, L.stream>>>(L.boxes, L.tiles, L.ntiles, L.zc, mode, part);
+  return cudaGetLastError();
+}
+
+template <typename T, int TY>
+static cudaError_t launch_lbp_t(const Launch& L, int mode, double* part) {
+  k_lbp<T, TY><<<L.grid, dim3(TX, TY), 0, L.stream>>>(L.boxes, L.tiles, L.ntiles, L.zc, mode, part);
+  return cudaGetLastError();
+}
+
+template <typename T, int TY>
 static cudaError_t launch_lc_t(const Launch& L, int mode, double* part) {
   k_lc<T, TY><<<L.grid, dim3(TX, TY), 0, L.stream>>>(L.boxes, L.tiles, L.ntiles, L.zc, mode, part);
   return cudaGetLastError();
@@ -1446,6 +1597,14 @@ cudaError_t launch_flb(int prec, const Launch& L, int mode, double* part) {
 cudaError_t launch_lc(int prec, const Launch& L, int mode, double* part) {
   if (prec == 0) { LCLB_DISPATCH_TY(launch_lc_t, float) }
   LCLB_DISPATCH_TY(launch_lc_t, double)
+}
+cudaError_t launch_stress(int prec, const Launch& L, int mode, double* part) {
+  if (prec == 0) { LCLB_DISPATCH_TY(launch_stress_t, float) }
+  LCLB_DISPATCH_TY(launch_stress_t, double)
+}
+cudaError_t launch_lbp(int prec, const Launch& L, int mode, double* part) {
+  if (prec == 0) { LCLB_DISPATCH_TY(launch_lbp_t, float) }
+  LCLB_DISPATCH_TY(launch_lbp_t, double)
 }
 
 cudaError_t launch_links(int prec, const DevBox* boxes, const int2* chunks, int nchunks, int grid, cudaStream_t s) {

@@ -230,6 +230,72 @@ def test_lc_off_and_flow_off_switches(P):
         compare(g, o, TOL64, ncol=1, radii=[3.5])
 
 
+# ------------------------------------------------------ step variants --
+# The force + LB part of a step runs as one fused kernel, as stress/force and
+# LB kernels on two streams, or as a stored-stress kernel followed by an LB
+# kernel taking the face divergence of the stored P; the autotuner picks one
+# per box-size signature, LCLB_VARIANT forces it.
+VARIANTS = ["fused", "split", "stored"]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_step_variants_ragged_cholesteric(P, monkeypatch, variant, prec):
+    monkeypatch.setenv("LCLB_VARIANT", variant)
+    L = (37, 29, 23)
+    p = dict(synth.NEMATIC, q0=2 * math.pi / 16)
+    cols = [dict(X=(17.3, 14.1, 11.6), a0=5.2, anchoring=1, w=0.02), dict(X=(4.4, 5.5, 6.6), a0=3.1)]
+    g, o = make_pair(P, L, p, P.LC_FP32 if prec == "f32" else P.LC_FP64, colloids=cols,
+                     init=("helix", 2, 1e-2, 11))
+    g.step(40)
+    o.step(40)
+    compare(g, o, TOL32 if prec == "f32" else TOL64, ncol=2, radii=[5.2, 3.1])
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_step_variants_walls_and_moving_colloid(P, monkeypatch, variant):
+    monkeypatch.setenv("LCLB_VARIANT", variant)
+    L = (24, 20, 18)
+    cols = [dict(X=(11.5, 9.5, 8.5), a0=4.0, anchoring=1, w=0.01, mobile=True, F_ext=(2e-4, 0.0, 1e-4))]
+    g, o = make_pair(P, L, dict(synth.NEMATIC), P.LC_FP32, wall_z=True, colloids=cols,
+                     init=("uniaxial", (0, 0, 1), 1e-3, 2))
+    g.step(60)
+    o.step(60)
+    compare(g, o, TOL32, ncol=1, radii=[4.0])
+    cols = [dict(X=(11.3, 9.6, 8.8), a0=3.6, anchoring=0, w=0.02, mobile=True)]
+    g, o = make_pair(P, L, dict(synth.NEMATIC), P.LC_FP64, colloids=cols, init=("uniaxial", (0, 1, 1), 1e-2, 3))
+    g.set_colloid_velocity(0, (0.02, -0.01, 0.015), (0.0, 0.002, 0.0))
+    o.set_colloid_velocity(0, (0.02, -0.01, 0.015), (0.0, 0.002, 0.0))
+    s0 = o.get_solid()
+    g.step(60)
+    o.step(60)
+    assert (o.get_solid() != s0).any()
+    compare(g, o, TOL64, ncol=1, radii=[3.6])
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_step_variants_lc_and_flow_switches(P, monkeypatch, variant):
+    monkeypatch.setenv("LCLB_VARIANT", variant)
+    L = (20, 16, 12)
+    for lc, flow in ((False, True), (True, False)):
+        p = dict(synth.NEMATIC)
+        g = P.Solver(*L, precision=P.LC_FP64, lc=lc, flow=flow, body_force=(1e-5, 0, 0), **p)
+        o = oracle.Oracle(*L, lc=lc, flow=flow, body_force=(1e-5, 0, 0), **p)
+        for s in (g, o):
+            s.init_uniaxial((0, 1, 1), amp=1e-2, seed=4)
+            s.add_colloid((9.5, 7.5, 5.5), 3.5, 1, 0.01)
+        g.step(20)
+        o.step(20)
+        compare(g, o, TOL64, ncol=1, radii=[3.5])
+
+
+def test_step_variant_override_rejects_unknown(P, monkeypatch):
+    monkeypatch.setenv("LCLB_VARIANT", "nonsense")
+    g = P.Solver(12, 12, 12, precision=P.LC_FP32, **synth.NEMATIC)
+    with pytest.raises(RuntimeError):
+        g.step(1)
+
+
 # ------------------------------------------------------------ invariants --
 def test_mass_and_momentum_fp32(P):
     L = (32, 32, 32)
