@@ -209,6 +209,11 @@ int lc_lb_profile(lc_lb* h, int nsteps, double ms_out[5]);
 int lc_lb_batch_profile(lc_lb_batch* b, int nsteps, double ms_out[5]);
 int lc_lb_profile_detail(lc_lb* h, int nsteps, double ms_out[8]);
 int lc_lb_batch_profile_detail(lc_lb_batch* b, int nsteps, double ms_out[8]);
+/* Number of kernel launches in one step as captured in the step's CUDA
+ * graph (autotunes and captures first if needed; the state does not
+ * advance). */
+int lc_lb_step_launches(lc_lb* h, int* n_out);
+int lc_lb_batch_step_launches(lc_lb_batch* b, int* n_out);
 int lc_lb_synchronize(lc_lb* h);
 const char* lc_lb_last_error(const lc_lb* h);
 const char* lc_lb_version(void);

@@ -134,6 +134,8 @@ def lib(use_torch_allocator: bool = True):
         L.lc_lb_batch_profile.argtypes = [vp, C.c_int, dp]
         L.lc_lb_profile_detail.argtypes = [vp, C.c_int, dp]
         L.lc_lb_batch_profile_detail.argtypes = [vp, C.c_int, dp]
+        L.lc_lb_step_launches.argtypes = [vp, ip]
+        L.lc_lb_batch_step_launches.argtypes = [vp, ip]
         L.lc_lb_synchronize.argtypes = [vp]
         L.lc_lb_last_error.argtypes = [vp]
         L.lc_lb_last_error.restype = C.c_char_p
@@ -339,6 +341,12 @@ class Solver:
     def synchronize(self):
         self._check(self.L.lc_lb_synchronize(self.h))
 
+    def step_launches(self) -> int:
+        """Kernel launches in one captured step."""
+        n = C.c_int()
+        self._check(self.L.lc_lb_step_launches(self.h, C.byref(n)))
+        return n.value
+
     def profile(self, n=10) -> dict:
         """Mean ms per step of each phase over n non-graph steps (advances the
         state), the step variant and its force + LB kernels."""
@@ -398,6 +406,11 @@ class Batch:
         self._check(self.L.lc_lb_batch_relax(self.h, float(tol), int(max_steps), int(check_every), C.byref(s),
                                              _dp(r)))
         return s.value, r
+
+    def step_launches(self) -> int:
+        n = C.c_int()
+        self._check(self.L.lc_lb_batch_step_launches(self.h, C.byref(n)))
+        return n.value
 
     def profile(self, n=10) -> dict:
         ms = np.empty(8)

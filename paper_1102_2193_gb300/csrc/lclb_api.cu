@@ -133,6 +133,7 @@ struct Group {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   bool dirty = true, tuned = false;
+  int graph_kernels = 0;  // kernel nodes of the captured step
   int nsm = 0;
   std::string err;
 };
@@ -826,6 +827,16 @@ int capture(Group* g) {
   CK(e, &g->err);
   g->graph = gr;
   CK(cudaGraphInstantiate(&g->gexec, gr, 0), &g->err);
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(gr, nullptr, &nn), &g->err);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) CK(cudaGraphGetNodes(gr, nodes.data(), &nn), &g->err);
+  g->graph_kernels = 0;
+  for (cudaGraphNode_t n : nodes) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(n, &t), &g->err);
+    if (t == cudaGraphNodeTypeKernel) ++g->graph_kernels;
+  }
   g->dirty = false;
   return LC_OK;
 }
@@ -1324,6 +1335,32 @@ int lc_lb_profile(lc_lb* h, int nsteps, double ms_out[5]) {
   if (!rc)
     for (int k = 0; k < 5; ++k) ms_out[k] = ms[k];
   return rc;
+}
+
+int lc_lb_step_launches(lc_lb* h, int* n_out) {
+  if (int rc = h_check(h)) return rc;
+  if (!n_out) return fail(&h->err, LC_ERR_ARG, "null output");
+  Group* g = h->g;
+  int rc = maybe_tune(g);
+  if (!rc) rc = capture(g);
+  if (rc) {
+    h->err = g->err;
+    return rc;
+  }
+  *n_out = g->graph_kernels;
+  return LC_OK;
+}
+
+int lc_lb_batch_step_launches(lc_lb_batch* b, int* n_out) {
+  if (!b || !n_out) return fail(b ? &b->err : nullptr, LC_ERR_ARG, "bad arguments");
+  int rc = maybe_tune(b->g);
+  if (!rc) rc = capture(b->g);
+  if (rc) {
+    b->err = b->g->err;
+    return rc;
+  }
+  *n_out = b->g->graph_kernels;
+  return LC_OK;
 }
 
 int lc_lb_batch_profile_detail(lc_lb_batch* b, int nsteps, double ms_out[8]) {

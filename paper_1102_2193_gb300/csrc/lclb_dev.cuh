@@ -231,10 +231,13 @@ __device__ void surface_q0(const DevBox& B, int c, int sx, int sy, int sz, const
     n[0] = T(0); n[1] = T(0); n[2] = T(1);
   } else {
     const DevColloid& C = B.col[c];
-    double d[3];
-    disp(B, (double)sx, (double)sy, (double)sz, C.X, d);
-    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    T s[3] = {T(d[0] / r), T(d[1] / r), T(d[2] / r)};
+    // the normal only orients Q0: the minimum-image offset is taken in FP64
+    // (positions up to the box size), its normalisation in T
+    double dd[3];
+    disp(B, (double)sx, (double)sy, (double)sz, C.X, dd);
+    const T d0 = T(dd[0]), d1 = T(dd[1]), d2 = T(dd[2]);
+    const T r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    T s[3] = {d0 / r, d1 / r, d2 / r};
     if (C.anchoring == 0) {
       n[0] = s[0]; n[1] = s[1]; n[2] = s[2];
     } else {

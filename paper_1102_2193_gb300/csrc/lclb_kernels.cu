@@ -83,6 +83,14 @@ __device__ __forceinline__ void load_box(DevBox& sb, const DevBox* boxes, int b)
   __syncthreads();
 }
 
+// Tile loops: reload the shared box record only when the tile's box changes
+// (b is uniform over the block, so the barriers are too).
+__device__ __forceinline__ void load_box(DevBox& sb, const DevBox* boxes, int b, int& cur) {
+  if (b == cur) return;
+  load_box(sb, boxes, b);
+  cur = b;
+}
+
 // ---------------------------------------------------------------------------
 // shared pieces of the force / LB kernels
 // ---------------------------------------------------------------------------
@@ -119,12 +127,14 @@ template <typename T>
 __device__ __forceinline__ void colloid_face(const DevBox& B, int c, int ax, T sgn, const T pcv[3], int x, int y,
                                              int kc, int& my_c, double my_acc[6]) {
   const DevColloid& C = B.col[c];
-  const double ff[3] = {-(double)sgn * (double)pcv[0], -(double)sgn * (double)pcv[1], -(double)sgn * (double)pcv[2]};
-  double r[3];
+  const T ff[3] = {-sgn * pcv[0], -sgn * pcv[1], -sgn * pcv[2]};
+  double rd[3];
   const double hx2 = 0.5 * (double)(ax == 0 ? sgn : 0), hy2 = 0.5 * (double)(ax == 1 ? sgn : 0),
                hz2 = 0.5 * (double)(ax == 2 ? sgn : 0);
-  disp(B, (double)x + hx2, (double)y + hy2, (double)kc + hz2, C.X, r);
-  const double tq[3] = {r[1] * ff[2] - r[2] * ff[1], r[2] * ff[0] - r[0] * ff[2], r[0] * ff[1] - r[1] * ff[0]};
+  disp(B, (double)x + hx2, (double)y + hy2, (double)kc + hz2, C.X, rd);
+  // the face force is in T; its moment arm from the FP64 offset, taken in T
+  const T r[3] = {T(rd[0]), T(rd[1]), T(rd[2])};
+  const T tq[3] = {r[1] * ff[2] - r[2] * ff[1], r[2] * ff[0] - r[0] * ff[2], r[0] * ff[1] - r[1] * ff[0]};
   if (my_c >= 0 && my_c != c) {  // a second colloid at this node: flush the first directly
     for (int a = 0; a < 6; ++a) {
       atomicAdd(&B.col[my_c].acc[6 + a], my_acc[a]);
@@ -134,8 +144,8 @@ __device__ __forceinline__ void colloid_face(const DevBox& B, int c, int ax, T s
   my_c = c;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    my_acc[a] += ff[a];
-    my_acc[3 + a] += tq[a];
+    my_acc[a] += (double)ff[a];
+    my_acc[3 + a] += (double)tq[a];
   }
 }
 
@@ -183,9 +193,10 @@ __global__ void __launch_bounds__(TX * TY) k_force(const DevBox* __restrict__ bo
   __shared__ double sred[32 * 1];
   const int tid = threadIdx.x + TX * threadIdx.y;
 
+  int cur_box = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
-    load_box(B, boxes, td.x);
+    load_box(B, boxes, td.x, cur_box);
     if (!B.p.lc_on) continue;
     const PhysT<T>& PP = phys<T>(B);
     int my_c = -1;
@@ -351,9 +362,10 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * 
     const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
     double* __restrict__ part) {
   __shared__ DevBox B;
+  int cur_box = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
-    load_box(B, boxes, td.x);
+    load_box(B, boxes, td.x, cur_box);
     if (!B.p.flow_on) continue;
     const PhysT<T>& PP = phys<T>(B);
     const int fpar = B.st->fpar;
@@ -395,9 +407,10 @@ template <typename T, int TY>
 __global__ void __launch_bounds__(TX * TY) k_stress(const DevBox* __restrict__ boxes, const int4* __restrict__ tiles,
                                                     int ntiles, int zc, int mode, double* __restrict__ part) {
   __shared__ DevBox B;
+  int cur_box = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
-    load_box(B, boxes, td.x);
+    load_box(B, boxes, td.x, cur_box);
     if (!B.p.lc_on) continue;
     const PhysT<T>& PP = phys<T>(B);
     const T* __restrict__ Q = static_cast<const T*>(B.Q[B.st->qpar]);
@@ -482,9 +495,10 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * 
     const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
     double* __restrict__ part) {
   __shared__ DevBox B;
+  int cur_box = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
-    load_box(B, boxes, td.x);
+    load_box(B, boxes, td.x, cur_box);
     if (!B.p.flow_on) continue;
     const PhysT<T>& PP = phys<T>(B);
     const int fpar = B.st->fpar;
@@ -553,9 +567,10 @@ __global__ void __launch_bounds__(32 * (BY + 3), (sizeof(T) == 4 && BY <= 4) ? 2
   const bool lbthread = tid >= 32 && tid < 32 * (BY + 1);
   const int tx = tid & 31, ty = (tid >> 5) - 1;
 
+  int cur_box = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
-    load_box(B, boxes, td.x);
+    load_box(B, boxes, td.x, cur_box);
     const PhysT<T>& PP = phys<T>(B);
     const bool lc = B.p.lc_on != 0, flow = B.p.flow_on != 0;
     if (!flow && !lc) continue;
@@ -621,9 +636,10 @@ __global__ void __launch_bounds__(TX * TY) k_lc(const DevBox* __restrict__ boxes
   __shared__ DevBox B;
   __shared__ double sred[32 * 2];
   const int tid = threadIdx.x + TX * threadIdx.y;
+  int cur_box = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
-    load_box(B, boxes, td.x);
+    load_box(B, boxes, td.x, cur_box);
     if (!B.p.lc_on) continue;
     const int qpar = B.st->qpar;
     const T* __restrict__ Q = static_cast<const T*>(B.Q[qpar]);
