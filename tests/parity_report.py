@@ -1,0 +1,73 @@
+"""Measured GPU-vs-oracle errors of the main parity cases, as a markdown table.
+
+    python tests/parity_report.py [--variant fused|split|stored] > report.md
+
+Runs the cases of test_gpu_parity.py (same inputs, same step counts) through
+the C ABI and the FP64 oracle and prints the maximum errors over fluid nodes
+and the colloid force / torque relative errors next to the tolerances the
+tests assert.  Needs a GPU.
+"""
+import argparse
+import math
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+sys.path.insert(0, HERE)
+
+import synth  # noqa: E402
+from test_gpu_parity import TOL32, TOL64, compare, make_pair  # noqa: E402
+
+
+def cases(P):
+    chol = dict(synth.NEMATIC, q0=2 * math.pi / 16)
+    two = [dict(X=(17.3, 14.1, 11.6), a0=5.2, anchoring=1, w=0.02), dict(X=(4.4, 5.5, 6.6), a0=3.1)]
+    w32 = synth.workload("nematic32")
+    w128 = synth.workload("chol128_R8")
+    yield ("nematic 32^3 planar colloid, 200 steps", "f64", w32["grid"], w32["params"], False, [w32["colloids"][0]],
+           ("uniaxial", w32["init"]["n"], w32["init"]["amp"], w32["init"]["seed"]), 200, None)
+    for prec in ("f32", "f64"):
+        yield (f"ragged 37x29x23 cholesteric, two colloids, 60 steps", prec, (37, 29, 23), chol, False, two,
+               ("helix", 2, 1e-2, 11), 60, None)
+        yield ("walls + mobile colloid with F_ext, 80 steps", prec, (24, 20, 18), dict(synth.NEMATIC), True,
+               [dict(X=(11.5, 9.5, 8.5), a0=4.0, anchoring=1, w=0.01, mobile=True, F_ext=(2e-4, 0.0, 1e-4))],
+               ("uniaxial", (0, 0, 1), 1e-3, 2), 80, None)
+        yield ("moving colloid, re-discretisation, 120 steps", prec, (24, 20, 18), dict(synth.NEMATIC), False,
+               [dict(X=(11.3, 9.6, 8.8), a0=3.6, anchoring=1, w=0.02, mobile=True)],
+               ("uniaxial", (0, 0, 1), 1e-2, 3), 120, (0.02, -0.01, 0.015))
+    yield ("128^3 cholesteric R = 8 (bench workload), 3 steps", "f32", w128["grid"], w128["params"], False,
+           [w128["colloids"][0]], ("helix", 2, w128["init"]["amp"], w128["init"]["seed"]), 3, None)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--variant", default=None)
+    a = ap.parse_args()
+    if a.variant:
+        os.environ["LCLB_VARIANT"] = a.variant
+    import paper_1102_2193_gb300 as P
+    P.lib()
+    print("| case | storage | max abs dQ | max abs du | max abs df | colloid force rel. | torque rel. |")
+    print("|---|---|---|---|---|---|---|")
+    for name, prec, L, prm, wall, cols, init, steps, vel in cases(P):
+        g, o = make_pair(P, L, prm, P.LC_FP32 if prec == "f32" else P.LC_FP64, wall_z=wall, colloids=cols,
+                         init=init, threads=16)
+        if vel is not None:
+            g.set_colloid_velocity(0, vel)
+            o.set_colloid_velocity(0, vel)
+        g.step(steps)
+        o.step(steps)
+        rep = {}
+        compare(g, o, TOL32 if prec == "f32" else TOL64, ncol=len(cols), report=rep, radii=[c["a0"] for c in cols])
+        fr = max(v for k, v in rep.items() if k.startswith("force"))
+        tr = max(v for k, v in rep.items() if k.startswith("torque"))
+        print(f"| {name} | {prec.upper()} | {rep['dQ']:.2e} | {rep['du']:.2e} | {rep['df']:.2e} | {fr:.2e} | {tr:.2e} |")
+        g.close()
+    tol = lambda t: f"dQ {t['Q']:g}, du {t['u']:g}, df {t['f']:g}, force {t['F']:g}"  # noqa: E731
+    print(f"\nTolerances asserted by the tests: FP32 {tol(TOL32)}; FP64 {tol(TOL64)} "
+          "(torque against the characteristic torque a0 (|F_hyd| + |F_LC|)).")
+
+
+if __name__ == "__main__":
+    main()
