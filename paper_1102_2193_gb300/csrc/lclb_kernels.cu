@@ -403,10 +403,59 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * 
 // stored-stress variant: k_stress stores H and P once per fluid node, k_lbp
 // takes the body force from the stored P
 // ---------------------------------------------------------------------------
+// Node i of the stored-stress kernel: gather (surface values at solid or wall
+// faces when near), H, P, stores, and for near nodes the colloid LC force.
+template <typename T, bool NEAR_NODE>
+__device__ __forceinline__ void stress_node(const DevBox& B, const PhysT<T>& PP, const T* __restrict__ Q,
+                                            T* __restrict__ Hb, T* __restrict__ Pb, int x, int y, int z, int i,
+                                            uint8_t m, int mode, int& my_c, double my_acc[6]) {
+  const int N = B.N;
+  T qi[5], qn[6][5], h[5], p[9], fp;
+  if (NEAR_NODE) {
+    gather_q(B, Q, x, y, z, i, m, qi, qn, nullptr);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) qi[k] = ldg(Q + (size_t)k * N + i);
+    int nb[6], zz[2];
+    face_neighbours(B, x, y, z, nb, zz);
+#pragma unroll
+    for (int d = 0; d < 6; ++d)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) qn[d][k] = ldg(Q + (size_t)k * N + nb[d]);
+  }
+  lc_node<T, true>(PP, qi, qn, h, p, &fp);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) Hb[(size_t)c * N + i] = h[c];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) Pb[(size_t)c * N + i] = p[c];
+  if (NEAR_NODE && (mode & FORCE_ACC)) {
+    int nb[6], zz[2];
+    face_neighbours(B, x, y, z, nb, zz);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const int j = nb[d];
+      if (j < 0) continue;
+      const uint8_t fj = B.mask[j] & IDMASK;
+      if (fj == 0) continue;
+      const int ax = d >> 1;
+      const T sgn = (d & 1) ? T(-1) : T(1);
+      const T pcv[3] = {p[ax], p[3 + ax], p[6 + ax]};
+      colloid_face(B, fj - 1, ax, sgn, pcv, x, y, z, my_c, my_acc);
+    }
+  }
+}
+
+// k_stress: H and P stored once per fluid node.  A warp evaluates its row's
+// nodes away from solids and walls together; nodes next to a solid or wall
+// (surface values, colloid faces) are queued per warp and evaluated 32 at a
+// time, so a row that crosses a colloid does not run the surface path with
+// most of its lanes idle.
 template <typename T, int TY>
 __global__ void __launch_bounds__(TX * TY) k_stress(const DevBox* __restrict__ boxes, const int4* __restrict__ tiles,
                                                     int ntiles, int zc, int mode, double* __restrict__ part) {
   __shared__ DevBox B;
+  __shared__ int sq[TY][2 * TX];  // per-warp queue of near fluid nodes
+  const int lane = threadIdx.x, wy = threadIdx.y;
   int cur_box = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
@@ -416,40 +465,41 @@ __global__ void __launch_bounds__(TX * TY) k_stress(const DevBox* __restrict__ b
     const T* __restrict__ Q = static_cast<const T*>(B.Q[B.st->qpar]);
     T* __restrict__ Hb = static_cast<T*>(B.H);
     T* __restrict__ Pb = static_cast<T*>(B.P);
-    const int nx = B.nx, ny = B.ny, N = B.N;
-    const int x = td.y + threadIdx.x, y = td.z + threadIdx.y;
+    const int nx = B.nx, ny = B.ny;
+    const int x = td.y + lane, y = td.z + wy;
     const int zend = min(td.w + zc, B.nz);
+    const bool valid = x < nx && y < ny;
     int my_c = -1;
     double my_acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    if (x < nx && y < ny) {
-      for (int z = td.w; z < zend; ++z) {
-        const int i = x + nx * (y + ny * z);
-        const uint8_t m = B.mask[i];
-        if (m & IDMASK) continue;
-        T qi[5], qn[6][5], h[5], p[9], fp;
-        gather_q(B, Q, x, y, z, i, m, qi, qn, nullptr);
-        lc_node<T, true>(PP, qi, qn, h, p, &fp);
-#pragma unroll
-        for (int c = 0; c < 5; ++c) Hb[(size_t)c * N + i] = h[c];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) Pb[(size_t)c * N + i] = p[c];
-        if ((mode & FORCE_ACC) && (m & NEAR)) {
-          int nb[6], zz[2];
-          face_neighbours(B, x, y, z, nb, zz);
-#pragma unroll
-          for (int d = 0; d < 6; ++d) {
-            const int j = nb[d];
-            if (j < 0) continue;
-            const uint8_t fj = B.mask[j] & IDMASK;
-            if (fj == 0) continue;
-            const int ax = d >> 1;
-            const T sgn = (d & 1) ? T(-1) : T(1);
-            const T pcv[3] = {p[ax], p[3 + ax], p[6 + ax]};
-            colloid_face(B, fj - 1, ax, sgn, pcv, x, y, z, my_c, my_acc);
-          }
+    int nq = 0;  // queued near nodes of this warp (warp-uniform)
+    for (int z = td.w; z < zend; ++z) {
+      const int i = x + nx * (y + ny * z);
+      const uint8_t m = valid ? B.mask[i] : (uint8_t)1;
+      const bool fluid = (m & IDMASK) == 0;
+      const bool near = fluid && (m & NEAR);
+      if (fluid && !near) stress_node<T, false>(B, PP, Q, Hb, Pb, x, y, z, i, m, mode, my_c, my_acc);
+      const unsigned nb = __ballot_sync(0xffffffffu, near);
+      if (nb) {
+        if (near) sq[wy][nq + __popc(nb & ((1u << lane) - 1u))] = i;
+        nq += __popc(nb);
+        __syncwarp();
+        if (nq >= TX) {
+          const int j = sq[wy][lane];
+          const int jx = j % nx, jy = (j / nx) % ny, jz = j / (nx * ny);
+          stress_node<T, true>(B, PP, Q, Hb, Pb, jx, jy, jz, j, B.mask[j], mode, my_c, my_acc);
+          __syncwarp();
+          nq -= TX;
+          if (lane < nq) sq[wy][lane] = sq[wy][TX + lane];
+          __syncwarp();
         }
       }
     }
+    if (lane < nq) {
+      const int j = sq[wy][lane];
+      const int jx = j % nx, jy = (j / nx) % ny, jz = j / (nx * ny);
+      stress_node<T, true>(B, PP, Q, Hb, Pb, jx, jy, jz, j, B.mask[j], mode, my_c, my_acc);
+    }
+    __syncwarp();
     if (mode & FORCE_ACC) warp_flush_colloid(B.col, my_c, my_acc, 6);
   }
 }
@@ -490,11 +540,37 @@ __device__ __forceinline__ void stored_force(const DevBox& B, const T* __restric
   }
 }
 
+// One fluid node of k_lbp: pull (bounce-back only for near nodes), body force
+// from the stored P, collide, store.  For a plain node the mask handed down
+// has the near bit cleared, which removes the neighbour checks at compile time.
+template <typename T, bool NEAR_NODE>
+__device__ __forceinline__ void lbp_node(const DevBox& B, const PhysT<T>& PP, const T* __restrict__ fin,
+                                         T* __restrict__ fout, const T* __restrict__ Pb, T* __restrict__ ub, int x,
+                                         int y, int z, int i, uint8_t m, bool pre, bool lc) {
+  const uint8_t mm = NEAR_NODE ? m : (uint8_t)(m & (uint8_t)~NEAR);
+  T df[NQ];
+  pull(B, fin, x, y, z, i, mm, pre, df);
+  T Fx = PP.g[0], Fy = PP.g[1], Fz = PP.g[2];
+  if (lc) {
+    T Fv[3];
+    stored_force(B, Pb, x, y, z, i, mm, Fv);
+    Fx += Fv[0];
+    Fy += Fv[1];
+    Fz += Fv[2];
+  }
+  collide_store(PP, fout, ub, B.N, i, df, Fx, Fy, Fz);
+}
+
+// k_lbp: like k_stress, a warp collides the plain fluid nodes of its row
+// together and queues the nodes next to a solid or wall (bounce-back links,
+// solid faces of the force) in shared memory, 32 at a time.
 template <typename T, int TY>
 __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * TY)) k_lbp(
     const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
     double* __restrict__ part) {
   __shared__ DevBox B;
+  __shared__ int sq[TY][2 * TX];
+  const int lane = threadIdx.x, wy = threadIdx.y;
   int cur_box = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
@@ -507,30 +583,39 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * 
     T* __restrict__ fout = static_cast<T*>(B.f[fpar ^ 1]);
     const T* __restrict__ Pb = static_cast<const T*>(B.P);
     T* __restrict__ ub = static_cast<T*>(B.u);
-    const int nx = B.nx, ny = B.ny, N = B.N;
-    const int x = td.y + threadIdx.x, y = td.z + threadIdx.y;
+    const int nx = B.nx, ny = B.ny;
+    const int x = td.y + lane, y = td.z + wy;
     const int zend = min(td.w + zc, B.nz);
-    if (x >= nx || y >= ny) continue;
+    const bool valid = x < nx && y < ny;
     const bool lc = B.p.lc_on != 0;
+    int nq = 0;
     for (int z = td.w; z < zend; ++z) {
       const int i = x + nx * (y + ny * z);
-      const uint8_t m = B.mask[i];
-      if (m & IDMASK) {
-        solid_velocity(B, ub, x, y, z, i, m);
-        continue;
+      const uint8_t m = valid ? B.mask[i] : (uint8_t)0;
+      const bool fluid = valid && (m & IDMASK) == 0;
+      const bool near = fluid && (m & NEAR);
+      if (valid && !fluid) solid_velocity(B, ub, x, y, z, i, m);
+      if (fluid && !near) lbp_node<T, false>(B, PP, fin, fout, Pb, ub, x, y, z, i, m, pre, lc);
+      const unsigned nb = __ballot_sync(0xffffffffu, near);
+      if (nb) {
+        if (near) sq[wy][nq + __popc(nb & ((1u << lane) - 1u))] = i;
+        nq += __popc(nb);
+        __syncwarp();
+        if (nq >= TX) {
+          const int j = sq[wy][lane];
+          lbp_node<T, true>(B, PP, fin, fout, Pb, ub, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j], pre, lc);
+          __syncwarp();
+          nq -= TX;
+          if (lane < nq) sq[wy][lane] = sq[wy][TX + lane];
+          __syncwarp();
+        }
       }
-      T df[NQ];
-      pull(B, fin, x, y, z, i, m, pre, df);
-      T Fx = PP.g[0], Fy = PP.g[1], Fz = PP.g[2];
-      if (lc) {
-        T Fv[3];
-        stored_force(B, Pb, x, y, z, i, m, Fv);
-        Fx += Fv[0];
-        Fy += Fv[1];
-        Fz += Fv[2];
-      }
-      collide_store(PP, fout, ub, N, i, df, Fx, Fy, Fz);
     }
+    if (lane < nq) {
+      const int j = sq[wy][lane];
+      lbp_node<T, true>(B, PP, fin, fout, Pb, ub, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j], pre, lc);
+    }
+    __syncwarp();
   }
 }
 

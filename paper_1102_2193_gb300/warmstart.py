@@ -177,15 +177,17 @@ def main(argv=None):
     ap.add_argument("--tol64", type=float, default=None)
     ap.add_argument("--eval", type=int, default=2, help="held-out geometries compared at S")
     ap.add_argument("--big", action="store_true", help="also compare at 2S: R = 12, p = 32")
+    ap.add_argument("--big-tol64", type=float, default=None, help="FP64 tolerance of the 2S case (default: FP32 only)")
     ap.add_argument("--seed", type=int, default=1000)
     a = ap.parse_args(argv)
     t0 = time.perf_counter()
     specs = geometries(a.train + a.hold, a.S, a.seed)
     data = relaxed_dataset(specs, a.S, a.relax_steps, torch)
     t_data = time.perf_counter() - t0
+    print(f"dataset: {len(data)} relaxed boxes in {t_data:.1f} s", flush=True)
     net = UNet(S=a.S, seed=a.seed)
     t1 = time.perf_counter()
-    hist = train(net, data[:a.train], a.epochs, a.lr, log=print)
+    hist = train(net, data[:a.train], a.epochs, a.lr, log=lambda m: print(m, flush=True))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
     res = dict(n_params=net.n_params(), data_s=t_data, train_s=t_train, train_loss=hist,
@@ -194,10 +196,13 @@ def main(argv=None):
     # the loss of the plain helix start on the held-out set (network output zero)
     zero = UNet(S=a.S, seed=a.seed)
     res["holdout_loss_identity"] = evaluate_loss(zero, data[a.train:])
-    for sp in specs[a.train:a.train + a.eval]:
-        res["cases"].append(compare(net, sp, a.S, torch, a.tol32, a.tol64))
+    print(json.dumps(dict(res, cases=None), default=float), flush=True)
+    todo = [(sp, a.S, a.tol64) for sp in specs[a.train:a.train + a.eval]]
     if a.big:
-        res["cases"].append(compare(net, dict(R=12.0, pitch=32.0, w=0.02), 2 * a.S, torch, a.tol32, a.tol64))
+        todo.append((dict(R=12.0, pitch=32.0, w=0.02), 2 * a.S, a.big_tol64))
+    for sp, S, tol64 in todo:
+        res["cases"].append(compare(net, sp, S, torch, a.tol32, tol64))
+        print(json.dumps(dict(case=res["cases"][-1]), default=float), flush=True)
     print(json.dumps(res, default=float), flush=True)
     return res
 

@@ -74,6 +74,7 @@ def compare(g, o, tol, ncol=0, report=None, radii=None):
             ok, d, n = _vec_err(cg[keys[0]] + cg[keys[1]], co[keys[0]] + co[keys[1]], rt, tol["Fabs"] + extra)
             if report is not None:
                 report[f"{name}{c}_rel"] = d / max(n, 1e-300)
+                report[f"{name}{c}_char"] = d / max(n + extra / max(rt, 1e-300), 1e-300)
             assert ok, f"colloid {c} total {name}: |diff| {d:.3e} vs |ref| {n:.3e}"
         for k in ("F_hyd", "F_lc", "T_hyd", "T_lc", "V", "X"):
             extra = tol["Fpart"] * tscale if k[0] == "T" else 0.0
