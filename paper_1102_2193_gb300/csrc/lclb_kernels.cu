@@ -715,12 +715,119 @@ __global__ void __launch_bounds__(32 * (BY + 3), (sizeof(T) == 4 && BY <= 4) ? 2
 // ---------------------------------------------------------------------------
 // k_lc: Beris-Edwards update
 // ---------------------------------------------------------------------------
+// Beris-Edwards update of fluid node i (Eq. 2): co-rotation from the central
+// velocity gradient, upwind advective fluxes through the faces (zero across
+// solid or wall faces, which only near nodes have), H stored by the stress
+// kernel of this step; Q^{n+1} stored, residual folded into (rsum, rmax).
+template <typename T, bool NEAR_NODE>
+__device__ __forceinline__ void lc_update_node(const DevBox& B, const PhysT<T>& PP, const T* __restrict__ Q,
+                                               T* __restrict__ Qo, const T* __restrict__ U, int x, int y, int z,
+                                               int i, uint8_t m, T& rsum, T& rmax) {
+  const int N = B.N;
+  const T Gam = PP.Gamma, xi = PP.xi;
+  // H of this node was stored by the stress kernel of this step; Q of the
+  // fluid face neighbours is needed only for the advective fluxes (zero
+  // across solid faces), so no surface values are formed here
+  const T* __restrict__ Hb = static_cast<const T*>(B.H);
+  T qi[5], qn[6][5], h[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    qi[c] = ldg(Q + (size_t)c * N + i);
+    h[c] = Hb[(size_t)c * N + i];
+  }
+  int nb[6], zz[2];
+  face_neighbours(B, x, y, z, nb, zz);
+  T ui[3], un[6][3];
+  bool fl[6];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) ui[a] = ldg(U + (size_t)a * N + i);
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const int j = nb[d];
+    fl[d] = !NEAR_NODE || (j >= 0 && (B.mask[j] & IDMASK) == 0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) un[d][a] = (!NEAR_NODE || j >= 0) ? ldg(U + (size_t)a * N + j) : T(0);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) qn[d][c] = fl[d] ? ldg(Q + (size_t)c * N + j) : T(0);
+  }
+  // velocity gradient W_ab = d_b u_a
+  T W[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) W[a][b] = T(0.5) * (un[2 * b][a] - un[2 * b + 1][a]);
+  // advective fluxes through the six faces (zero across solid faces)
+  T adv[5] = {T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    if (!fl[d]) continue;
+    const int ax = d >> 1;
+    const T uf = T(0.5) * (ui[ax] + un[d][ax]);
+    const bool plus = (d & 1) == 0;
+    // + face: upwind is i when uf > 0; - face: upwind is the neighbour when uf > 0
+    const bool take_i = plus ? (uf > T(0)) : !(uf > T(0));
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const T fl_ = uf * (take_i ? qi[k] : qn[d][k]);
+      adv[k] += plus ? fl_ : -fl_;
+    }
+  }
+  // co-rotation S = xi (D Qt + Qt D) + (Om Q - Q Om) - 2 xi Qt Tr(Q W), Qt = Q + I/3
+  T D[3][3], Om[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      D[a][b] = T(0.5) * (W[a][b] + W[b][a]);
+      Om[a][b] = T(0.5) * (W[a][b] - W[b][a]);
+    }
+  T trQW = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) trQW += qab(qi, a, b) * D[a][b];
+  T dQ[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T s = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        s += xi * (D[a][c] * qab(qi, c, b) + qab(qi, a, c) * D[c][b]) + Om[a][c] * qab(qi, c, b) -
+             qab(qi, a, c) * Om[c][b];
+      s += xi * T(2) / T(3) * D[a][b];
+      s -= T(2) * xi * (qab(qi, a, b) + (a == b ? T(1) / T(3) : T(0))) * trQW;
+      dQ[a][b] = s;
+    }
+  const T tr = dQ[0][0] + dQ[1][1] + dQ[2][2];
+  const int ia[5] = {0, 0, 0, 1, 1}, ib[5] = {0, 1, 2, 1, 2};
+  T d5[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    T v = Gam * h[k] + dQ[ia[k]][ib[k]] - adv[k];
+    if (ia[k] == ib[k]) v -= tr / T(3);
+    d5[k] = v;
+    Qo[(size_t)k * N + i] = qi[k] + v;
+  }
+  const T dzz = -d5[0] - d5[3];
+  rsum += d5[0] * d5[0] + d5[3] * d5[3] + dzz * dzz + T(2) * (d5[1] * d5[1] + d5[2] * d5[2] + d5[4] * d5[4]);
+  T mx = fabs(dzz);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) mx = fmax(mx, fabs(d5[k]));
+  rmax = fmax(rmax, mx);
+}
+
+// k_lc: Beris-Edwards update; plain nodes of a warp's row together, nodes
+// next to a solid or wall queued and updated 32 at a time.
 template <typename T, int TY>
 __global__ void __launch_bounds__(TX * TY) k_lc(const DevBox* __restrict__ boxes, const int4* __restrict__ tiles,
                                                 int ntiles, int zc, int mode, double* __restrict__ part) {
   __shared__ DevBox B;
   __shared__ double sred[32 * 2];
+  __shared__ int sq[TY][2 * TX];
   const int tid = threadIdx.x + TX * threadIdx.y;
+  const int lane = threadIdx.x, wy = threadIdx.y;
   int cur_box = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
@@ -730,111 +837,39 @@ __global__ void __launch_bounds__(TX * TY) k_lc(const DevBox* __restrict__ boxes
     const T* __restrict__ Q = static_cast<const T*>(B.Q[qpar]);
     T* __restrict__ Qo = static_cast<T*>(B.Q[qpar ^ 1]);
     const T* __restrict__ U = static_cast<const T*>(B.u);
-    const int nx = B.nx, ny = B.ny, N = B.N;
-    const int x = td.y + threadIdx.x, y = td.z + threadIdx.y;
+    const int nx = B.nx, ny = B.ny;
+    const int x = td.y + lane, y = td.z + wy;
     const int zend = min(td.w + zc, B.nz);
     const bool valid = x < nx && y < ny;
     const PhysT<T>& PP = phys<T>(B);
-    const T Gam = PP.Gamma, xi = PP.xi;
     T rsum = T(0), rmax = T(0);  // per-thread residual (sum of squares, max), in T
-    if (valid) {
-      for (int z = td.w; z < zend; ++z) {
-        const int i = x + nx * (y + ny * z);
-        const uint8_t m = B.mask[i];
-        if (m & IDMASK) continue;
-        // H of this node was stored by the stress kernel of this step; Q of the
-        // fluid face neighbours is needed only for the advective fluxes (zero
-        // across solid faces), so no surface values are formed here
-        const T* __restrict__ Hb = static_cast<const T*>(B.H);
-        T qi[5], qn[6][5], h[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          qi[c] = ldg(Q + (size_t)c * N + i);
-          h[c] = Hb[(size_t)c * N + i];
+    int nq = 0;
+    for (int z = td.w; z < zend; ++z) {
+      const int i = x + nx * (y + ny * z);
+      const uint8_t m = valid ? B.mask[i] : (uint8_t)1;
+      const bool fluid = (m & IDMASK) == 0;
+      const bool near = fluid && (m & NEAR);
+      if (fluid && !near) lc_update_node<T, false>(B, PP, Q, Qo, U, x, y, z, i, m, rsum, rmax);
+      const unsigned nb = __ballot_sync(0xffffffffu, near);
+      if (nb) {
+        if (near) sq[wy][nq + __popc(nb & ((1u << lane) - 1u))] = i;
+        nq += __popc(nb);
+        __syncwarp();
+        if (nq >= TX) {
+          const int j = sq[wy][lane];
+          lc_update_node<T, true>(B, PP, Q, Qo, U, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j], rsum, rmax);
+          __syncwarp();
+          nq -= TX;
+          if (lane < nq) sq[wy][lane] = sq[wy][TX + lane];
+          __syncwarp();
         }
-        int nb[6], zz[2];
-        face_neighbours(B, x, y, z, nb, zz);
-        T ui[3], un[6][3];
-        bool fl[6];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) ui[a] = ldg(U + (size_t)a * N + i);
-#pragma unroll
-        for (int d = 0; d < 6; ++d) {
-          const int j = nb[d];
-          fl[d] = j >= 0 && (!(m & NEAR) || (B.mask[j] & IDMASK) == 0);
-#pragma unroll
-          for (int a = 0; a < 3; ++a) un[d][a] = j >= 0 ? ldg(U + (size_t)a * N + j) : T(0);
-#pragma unroll
-          for (int c = 0; c < 5; ++c) qn[d][c] = fl[d] ? ldg(Q + (size_t)c * N + j) : T(0);
-        }
-        // velocity gradient W_ab = d_b u_a
-        T W[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) W[a][b] = T(0.5) * (un[2 * b][a] - un[2 * b + 1][a]);
-        // advective fluxes through the six faces (zero across solid faces)
-        T adv[5] = {T(0), T(0), T(0), T(0), T(0)};
-#pragma unroll
-        for (int d = 0; d < 6; ++d) {
-          if (!fl[d]) continue;
-          const int ax = d >> 1;
-          const T uf = T(0.5) * (ui[ax] + un[d][ax]);
-          const bool plus = (d & 1) == 0;
-          // + face: upwind is i when uf > 0; - face: upwind is the neighbour when uf > 0
-          const bool take_i = plus ? (uf > T(0)) : !(uf > T(0));
-#pragma unroll
-          for (int k = 0; k < 5; ++k) {
-            const T fl_ = uf * (take_i ? qi[k] : qn[d][k]);
-            adv[k] += plus ? fl_ : -fl_;
-          }
-        }
-        // co-rotation S = xi (D Qt + Qt D) + (Om Q - Q Om) - 2 xi Qt Tr(Q W), Qt = Q + I/3
-        T D[3][3], Om[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) {
-            D[a][b] = T(0.5) * (W[a][b] + W[b][a]);
-            Om[a][b] = T(0.5) * (W[a][b] - W[b][a]);
-          }
-        T trQW = T(0);
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) trQW += qab(qi, a, b) * D[a][b];
-        T dQ[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) {
-            T s = T(0);
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-              s += xi * (D[a][c] * qab(qi, c, b) + qab(qi, a, c) * D[c][b]) + Om[a][c] * qab(qi, c, b) -
-                   qab(qi, a, c) * Om[c][b];
-            s += xi * T(2) / T(3) * D[a][b];
-            s -= T(2) * xi * (qab(qi, a, b) + (a == b ? T(1) / T(3) : T(0))) * trQW;
-            dQ[a][b] = s;
-          }
-        const T tr = dQ[0][0] + dQ[1][1] + dQ[2][2];
-        const int ia[5] = {0, 0, 0, 1, 1}, ib[5] = {0, 1, 2, 1, 2};
-        T d5[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-          T v = Gam * h[k] + dQ[ia[k]][ib[k]] - adv[k];
-          if (ia[k] == ib[k]) v -= tr / T(3);
-          d5[k] = v;
-          Qo[(size_t)k * N + i] = qi[k] + v;
-        }
-        const T dzz = -d5[0] - d5[3];
-        rsum += d5[0] * d5[0] + d5[3] * d5[3] + dzz * dzz + T(2) * (d5[1] * d5[1] + d5[2] * d5[2] + d5[4] * d5[4]);
-        T mx = fabs(dzz);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) mx = fmax(mx, fabs(d5[k]));
-        rmax = fmax(rmax, mx);
       }
     }
+    if (lane < nq) {
+      const int j = sq[wy][lane];
+      lc_update_node<T, true>(B, PP, Q, Qo, U, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j], rsum, rmax);
+    }
+    __syncwarp();
     if (mode & LC_RESID) {
       double rs[2] = {(double)rsum, (double)rmax};
       block_sum<2>(rs, sred, true);
