@@ -77,9 +77,15 @@ __device__ __forceinline__ void warp_flush_colloid(DevColloid* col, int c, const
   }
 }
 
+// The block's shared copy of box b's record, copied by all threads in 4-byte
+// words (DevBox is a multiple of 8 bytes and 8-byte aligned).
+static_assert(sizeof(DevBox) % 4 == 0, "DevBox is copied in 4-byte words");
 __device__ __forceinline__ void load_box(DevBox& sb, const DevBox* boxes, int b) {
   __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) sb = boxes[b];
+  const unsigned* src = reinterpret_cast<const unsigned*>(boxes + b);
+  unsigned* dst = reinterpret_cast<unsigned*>(&sb);
+  const int nthr = blockDim.x * blockDim.y;
+  for (int k = threadIdx.x + blockDim.x * threadIdx.y; k < (int)(sizeof(DevBox) / 4); k += nthr) dst[k] = src[k];
   __syncthreads();
 }
 
