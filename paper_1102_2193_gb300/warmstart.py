@@ -6,10 +6,14 @@
    the inputs (solid map, helix Q) and the relaxed Q stay on the device.
 2. ``train``: the U-Net of ``surrogate`` is fitted to them with its own
    forward/backward kernels and Adam.
-3. ``propose`` / ``compare``: the network's Q (trilinearly upsampled when the
-   target box is twice the network's) replaces the helix as the start, and
-   the plain relaxation, which decides acceptance and is the fallback, is run from
-   both starts; steps, wall time, residual and free energy are reported.
+3. ``propose`` / ``compare``: the network's Q (for a box twice the
+   training size, the same weights run on the full-size geometry, or on the
+   halved geometry with a trilinear upsample) replaces the helix as the
+   start, and the plain relaxation, which decides acceptance and is the
+   fallback, is run from both starts; steps, wall time (inference included),
+   residual and free energy are reported.
+4. ``batched_vs_single``: the same boxes relaxed one handle at a time and as
+   one batch.
 
 The relaxation runs with the flow frozen (u = 0): the statics do not depend on
 it, and with the paper's constants the coupled flow at tau = 2.5 is unstable.
@@ -97,11 +101,27 @@ def evaluate_loss(net: UNet, data) -> float:
     return tot / len(data)
 
 
-def propose(net: UNet, spec, S_target: int, torch):
-    """Network Q for a box of size S_target (= net.S or 2 net.S); in the
-    second case the network sees the geometry halved and its output is
-    trilinearly upsampled (the 5-component storage stays traceless)."""
+def propose(net: UNet, spec, S_target: int, torch, mode: str = "direct"):
+    """Network Q for a box of size S_target.  At S_target = net.S the network
+    sees the box itself.  At S_target = 2 net.S, ``mode="direct"`` runs the
+    same weights on the full-size geometry (every layer is a periodic
+    convolution, so the network applies to any S divisible by 4) and
+    ``mode="upsample"`` runs it on the geometry halved (R/2, p/2) and
+    trilinearly upsamples the output (the 5-component storage stays
+    traceless)."""
     scale = S_target // net.S
+    if scale == 2 and mode == "direct":
+        big = UNet(S=S_target, seed=0)
+        big.load(net.state())
+        tmp = Solver(S_target, S_target, S_target, precision=LC_FP32, **_params(spec))
+        _setup(tmp, spec, S_target)
+        solid, q0 = solver_fields(tmp, torch)
+        big.set_input(solid, q0, spec["R"], spec["pitch"], spec["w"])
+        big.forward()
+        q = big.predict_soa()
+        tmp.close()
+        del big
+        return q
     s = dict(spec, R=spec["R"] / scale, pitch=spec["pitch"] / scale)
     tmp = Solver(net.S, net.S, net.S, precision=LC_FP32, **_params(s))
     _setup(tmp, s, net.S)
@@ -147,16 +167,55 @@ def relax_from(spec, S, q_start, tol_fp32, tol, torch, max_steps=2_000_000, chec
     return out
 
 
-def compare(net: UNet, spec, S, torch, tol_fp32=3e-8, tol=1e-8, max_steps=2_000_000):
-    q_warm = propose(net, spec, S, torch)
-    plain = relax_from(spec, S, None, tol_fp32, tol, torch, max_steps)
+def compare(net: UNet, spec, S, torch, tol_fp32=3e-8, tol=1e-8, max_steps=2_000_000, mode="direct", plain=None):
+    """Relax from the helix (``plain``, when given, is a result of an earlier
+    relaxation of the same case) and from the network's proposal."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    q_warm = propose(net, spec, S, torch, mode)
+    torch.cuda.synchronize()
+    t_propose = time.perf_counter() - t0
+    if plain is None:
+        plain = relax_from(spec, S, None, tol_fp32, tol, torch, max_steps)
     warm = relax_from(spec, S, q_warm, tol_fp32, tol, torch, max_steps)
+    warm["time_propose"] = t_propose  # network inference is part of the warm start's wall time
+    warm["time"] += t_propose
     use_warm = warm["free_energy"] <= plain["free_energy"] + 1e-4 * abs(plain["free_energy"])
-    return dict(spec=spec, S=S, plain=plain, warm=warm, warm_accepted=bool(use_warm),
+    return dict(spec=spec, S=S, mode=mode if S != net.S else "native", plain=plain, warm=warm,
+                warm_accepted=bool(use_warm),
                 speedup_steps=(plain["steps_fp32"] + plain["steps_fp64"]) /
                 max(1, warm["steps_fp32"] + warm["steps_fp64"]),
                 speedup_time=plain["time"] / max(warm["time"], 1e-9),
                 free_energy_rel=(warm["free_energy"] - plain["free_energy"]) / abs(plain["free_energy"]))
+
+
+def batched_vs_single(specs, S, torch, tol_fp32=3e-8, max_steps=2_000_000, check=1000):
+    """Relax the boxes of ``specs`` one after another, each with its own
+    handle, and then all together as one batch (one launch per phase and
+    step for every box); returns both wall times and, per box, the steps,
+    residual and free energy of either route."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    single = [relax_from(sp, S, None, tol_fp32, None, torch, max_steps, check) for sp in specs]
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    B = Batch([dict(grid=(S, S, S), params=_params(sp)) for sp in specs], precision=LC_FP32)
+    try:
+        for box, sp in zip(B.boxes, specs):
+            _setup(box, sp, S)
+        steps, resid = B.relax(tol=tol_fp32, max_steps=max_steps, check_every=check)
+        diags = [box.diag() for box in B.boxes]
+    finally:
+        B.close()
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t1
+    rel = [abs(d["free_energy"] - s["free_energy"]) / abs(s["free_energy"]) for d, s in zip(diags, single)]
+    return dict(S=S, boxes=len(specs), tol=tol_fp32, time_single=t_single, time_batch=t_batch,
+                speedup=t_single / max(t_batch, 1e-9), steps_single=[s["steps_fp32"] for s in single],
+                steps_batch=int(steps), resid_batch=[float(r) for r in resid],
+                resid_single=[s["resid"] for s in single], free_energy_rel_max=max(rel),
+                defects_equal=all(d["n_defect"] == s["n_defect"] for d, s in zip(diags, single)))
 
 
 def main(argv=None):
@@ -178,6 +237,9 @@ def main(argv=None):
     ap.add_argument("--eval", type=int, default=2, help="held-out geometries compared at S")
     ap.add_argument("--big", action="store_true", help="also compare at 2S: R = 12, p = 32")
     ap.add_argument("--big-tol64", type=float, default=None, help="FP64 tolerance of the 2S case (default: FP32 only)")
+    ap.add_argument("--big-mode", default="direct", choices=("direct", "upsample", "both"))
+    ap.add_argument("--batch-compare", type=int, default=0, help="also relax this many held-out boxes one by one "
+                    "and as one batch")
     ap.add_argument("--seed", type=int, default=1000)
     a = ap.parse_args(argv)
     t0 = time.perf_counter()
@@ -197,12 +259,21 @@ def main(argv=None):
     zero = UNet(S=a.S, seed=a.seed)
     res["holdout_loss_identity"] = evaluate_loss(zero, data[a.train:])
     print(json.dumps(dict(res, cases=None), default=float), flush=True)
-    todo = [(sp, a.S, a.tol64) for sp in specs[a.train:a.train + a.eval]]
+    todo = [(sp, a.S, a.tol64, "direct") for sp in specs[a.train:a.train + a.eval]]
     if a.big:
-        todo.append((dict(R=12.0, pitch=32.0, w=0.02), 2 * a.S, a.big_tol64))
-    for sp, S, tol64 in todo:
-        res["cases"].append(compare(net, sp, S, torch, a.tol32, tol64))
+        big = dict(R=12.0, pitch=32.0, w=0.02)
+        for mode in (("direct", "upsample") if a.big_mode == "both" else (a.big_mode,)):
+            todo.append((big, 2 * a.S, a.big_tol64, mode))
+    plain_of = {}
+    for sp, S, tol64, mode in todo:
+        key = (json.dumps(sp, sort_keys=True), S)
+        res["cases"].append(compare(net, sp, S, torch, a.tol32, tol64, mode=mode, plain=plain_of.get(key)))
+        plain_of[key] = res["cases"][-1]["plain"]
         print(json.dumps(dict(case=res["cases"][-1]), default=float), flush=True)
+    if a.batch_compare:
+        held = specs[a.train:a.train + a.batch_compare]
+        res["batched"] = batched_vs_single(held, a.S, torch, a.tol32)
+        print(json.dumps(dict(batched=res["batched"]), default=float), flush=True)
     print(json.dumps(res, default=float), flush=True)
     return res
 

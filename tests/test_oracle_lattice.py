@@ -4,6 +4,7 @@ Each test checks the oracle against something other than itself: published
 test vectors, library routines, or moment identities of the D3Q19 lattice.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -99,3 +100,47 @@ def test_dimensionless_groups_paper_values():
     assert abs(d["kappa"] - 0.3) < 1e-3
     d2 = dimensionless(A0=0.01, K=0.01, gamma=3.0, q0=2 * math.pi / 32, Gamma=0.5, q=0.5)
     assert abs(d2["kappa"] - 1.178) < 1e-3
+
+
+def _paper_values():
+    out = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_printed_values.txt")) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = (t.strip() for t in line.split("="))
+                out[k] = float(v)
+    return out
+
+
+def test_printed_parameters_fixture():
+    """The Sec. 2.1 parameter set reproduces the printed derived values: the
+    oracle's closed-form bulk order equals the printed q, the reduced
+    temperature and rotational viscosity (Eqs. 5-6) come out as printed, p = 32
+    gives the printed chirality to its printed digit, and the two printed drag
+    coefficients of Eq. 9 give the printed ratio within its uncertainty."""
+    from paper_1102_2193_gb300 import dimensionless
+    pv = _paper_values()
+    assert abs(oracle.bulk_q(pv["gamma"]) - pv["q"]) < 1e-15
+    d = dimensionless(A0=pv["A0"], K=pv["K"], gamma=pv["gamma"], q0=2 * math.pi / pv["pitch"], Gamma=pv["Gamma"],
+                      q=pv["q"])
+    assert abs(d["tau"] - pv["tau_reduced"]) < 1e-15
+    assert abs(d["gamma1"] - pv["gamma1"]) < 1e-15
+    assert round(d["kappa"], int(pv["kappa_printed_digits"])) == pv["kappa"]
+    assert abs(pv["a_perp"] / pv["a_par"] - pv["drag_ratio"]) <= pv["drag_ratio_err"]
+
+
+def test_defect_threshold_matches_printed_value():
+    """The defect count of the diagnostics uses the printed threshold: a
+    uniaxial Q of order just above it is not a defect, just below it is."""
+    pv = _paper_values()
+    thr = pv["defect_threshold"]
+    for S, expect in ((thr + 1e-6, 0), (thr - 1e-6, 1)):
+        o = oracle.Oracle(4, 4, 4, lc=False, flow=False)
+        n = np.array([0.0, 0.0, 1.0])
+        Qt = S * (np.outer(n, n) - np.eye(3) / 3)
+        Q = np.zeros((5, 4, 4, 4))
+        for k, (a, b) in enumerate(((0, 0), (0, 1), (0, 2), (1, 1), (1, 2))):
+            Q[k] = Qt[a, b]
+        o.set_Q(Q)
+        assert o.diag()["n_defect"] == expect * 64
