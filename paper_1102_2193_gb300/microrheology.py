@@ -5,9 +5,13 @@ far-field director is along z; its two boojums sit at the poles.  A constant
 force f is applied across the director (along x) in one box and along it
 (along z) in another; a third box, with no force, carries the drift of the
 colloid while its defect structure forms, which the drag estimate subtracts.
-The three boxes advance together as one batch (one launch per phase and
-step).  The drag law f = a v (Eq. 9) gives a_perp = f / v_x and
-a_par = f / v_z, and the anisotropy a_perp / a_par = v_z / v_x.
+Two more boxes repeat both pulls with the liquid-crystal stress switched
+off (an isotropic fluid of the same viscosity), which measures the part of
+the anisotropy that comes from the box geometry alone.  The five boxes
+advance together as one batch (one launch per phase and step).  The drag law
+f = a v (Eq. 9) gives a_perp = f / v_x and a_par = f / v_z, the anisotropy
+a_perp / a_par = v_z / v_x, and the anisotropy due to the nematic is that
+ratio divided by the isotropic one.
 
 Default geometry (``walls=True``): 64^3 with no-slip walls at z = -1/2 and
 nz - 1/2 anchoring the director along z, periodic in x and y; the walls take
@@ -33,16 +37,18 @@ NEMATIC = dict(rho0=1.0, tau=2.5, A0=0.01, gamma=3.0, K=0.01, q0=0.0, xi=0.7, Ga
 def micro_batch(L=64, R=8.0, force=1e-4, w=0.01, pulls=("x", "z", "none"), walls=True, params=None,
                 precision=LC_FP32, amp=1e-3, seed=2):
     """A batch of boxes that differ only in the pull direction (``pulls``:
-    "x", "y", "z" or "none"); director along z, one mobile planar colloid of
-    radius R at the box centre.  Returns the Batch (the caller closes it)."""
+    "x", "y", "z" or "none", with the suffix "_iso" for a box whose LC stress
+    is switched off); director along z, one mobile planar colloid of radius R
+    at the box centre.  Returns the Batch (the caller closes it)."""
     prm = dict(NEMATIC if params is None else params)
-    B = Batch([dict(grid=(L, L, L), wall_z=walls, params=prm) for _ in pulls], precision=precision)
+    B = Batch([dict(grid=(L, L, L), wall_z=walls, params=dict(prm, lc=not p.endswith("_iso"))) for p in pulls],
+              precision=precision)
     c = (L - 1) / 2.0
     axes = dict(x=0, y=1, z=2)
     for box, p in zip(B.boxes, pulls):
         F = [0.0, 0.0, 0.0]
-        if p != "none":
-            F[axes[p]] = force
+        if p.split("_")[0] != "none":
+            F[axes[p.split("_")[0]]] = force
         box.init_uniaxial((0.0, 0.0, 1.0), amp, seed)
         box.add_colloid((c, c, c), R, LC_PLANAR, w, mobile=True, F_ext=F)
     return B
@@ -55,7 +61,7 @@ def drag_anisotropy(L=64, R=8.0, force=1e-4, w=0.01, steps=20000, every=1000, wa
     last ``tail`` samples, the unpulled box's velocity subtracted) and the
     drag coefficients of Eq. 9."""
     prm = dict(NEMATIC if params is None else params)
-    pulls = ("x", "z", "none")
+    pulls = ("x", "z", "none", "x_iso", "z_iso")
     B = micro_batch(L, R, force, w, pulls, walls, prm, precision)
     try:
         series = {p: [] for p in pulls}
@@ -75,11 +81,15 @@ def drag_anisotropy(L=64, R=8.0, force=1e-4, w=0.01, steps=20000, every=1000, wa
         v_par = float(np.mean(S["z"][-k:, 2] - S["none"][-k:, 2]))
         v_perp_raw = float(np.mean(S["x"][-k:, 0]))
         v_par_raw = float(np.mean(S["z"][-k:, 2]))
+        v_perp_iso = float(np.mean(S["x_iso"][-k:, 0]))
+        v_par_iso = float(np.mean(S["z_iso"][-k:, 2]))
         eta = prm["rho0"] * (prm["tau"] - 0.5) / 3.0
         return dict(L=L, R=R, force=force, w=w, walls=walls, steps=steps, every=every, v_perp=v_perp, v_par=v_par,
                     a_perp=force / v_perp, a_par=force / v_par, ratio=v_par / v_perp,
-                    ratio_raw=v_par_raw / v_perp_raw, stokes_a=6.0 * math.pi * eta * R, wall_s=wall,
-                    lups=3 * L**3 * steps / wall, series={p: v for p, v in series.items()})
+                    ratio_raw=v_par_raw / v_perp_raw, a_perp_iso=force / v_perp_iso, a_par_iso=force / v_par_iso,
+                    ratio_iso=v_par_iso / v_perp_iso, ratio_nematic=(v_par / v_perp) / (v_par_iso / v_perp_iso),
+                    stokes_a=6.0 * math.pi * eta * R, wall_s=wall, lups=len(pulls) * L**3 * steps / wall,
+                    series={p: v for p, v in series.items()})
     finally:
         B.close()
 

@@ -31,12 +31,12 @@ from .surrogate import UNet, solver_fields, upsample2
 PAPER = dict(rho0=1.0, tau=2.5, A0=1.0, gamma=3.0, K=0.065, xi=0.7, Gamma=0.5)
 
 
-def geometries(n: int, S: int, seed: int) -> list:
-    """n seeded (R, pitch, w) with p in {16, 20, ..., 32}, R/p in [0.1, 0.6], w in [0.005, 0.05]."""
+def geometries(n: int, S: int, seed: int, pitches=(16, 20, 24, 28, 32)) -> list:
+    """n seeded (R, pitch, w) with p drawn from ``pitches``, R/p in [0.1, 0.6], w in [0.005, 0.05]."""
     rng = np.random.default_rng(seed)
     out = []
     while len(out) < n:
-        p = float(rng.choice([16, 20, 24, 28, 32]))
+        p = float(rng.choice(list(pitches)))
         R = float(rng.uniform(0.1, 0.6) * p)
         if not 3.0 <= R <= S / 4:
             continue
@@ -189,32 +189,57 @@ def compare(net: UNet, spec, S, torch, tol_fp32=3e-8, tol=1e-8, max_steps=2_000_
                 free_energy_rel=(warm["free_energy"] - plain["free_energy"]) / abs(plain["free_energy"]))
 
 
-def batched_vs_single(specs, S, torch, tol_fp32=3e-8, max_steps=2_000_000, check=1000):
+def _relax_one(spec, S, precision, tol, max_steps, check):
+    """One box relaxed on its own handle; returns steps, residual, wall time,
+    free energy and defect count."""
+    s = Solver(S, S, S, precision=precision, **_params(spec))
+    try:
+        _setup(s, spec, S)
+        n, r = s.relax(tol=tol, max_steps=max_steps, check_every=check)
+        d = s.diag()
+    finally:
+        s.close()
+    return dict(steps=int(n), resid=float(r), free_energy=d["free_energy"], n_defect=d["n_defect"])
+
+
+def commensurate_geometries(n: int, S: int, seed: int) -> list:
+    """Like :func:`geometries`, with pitches whose half (the period of Q)
+    divides S, so that the periodic box holds a whole number of Q periods and
+    the helix does not have to change its pitch while relaxing."""
+    return geometries(n, S, seed, pitches=[p for p in (16, 24, 32, 48, 64) if S % (p // 2) == 0])
+
+
+def batched_vs_single(specs, S, torch, tol=1e-8, precision=LC_FP64, max_steps=400_000, check=1000, log=None):
     """Relax the boxes of ``specs`` one after another, each with its own
     handle, and then all together as one batch (one launch per phase and
     step for every box); returns both wall times and, per box, the steps,
     residual and free energy of either route."""
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    single = [relax_from(sp, S, None, tol_fp32, None, torch, max_steps, check) for sp in specs]
+    single = []
+    for sp in specs:
+        single.append(_relax_one(sp, S, precision, tol, max_steps, check))
+        if log:
+            log(f"single {len(single)}/{len(specs)}: {single[-1]} ({time.perf_counter() - t0:.1f} s)")
     torch.cuda.synchronize()
     t_single = time.perf_counter() - t0
     t1 = time.perf_counter()
-    B = Batch([dict(grid=(S, S, S), params=_params(sp)) for sp in specs], precision=LC_FP32)
+    B = Batch([dict(grid=(S, S, S), params=_params(sp)) for sp in specs], precision=precision)
     try:
         for box, sp in zip(B.boxes, specs):
             _setup(box, sp, S)
-        steps, resid = B.relax(tol=tol_fp32, max_steps=max_steps, check_every=check)
+        steps, resid = B.relax(tol=tol, max_steps=max_steps, check_every=check)
         diags = [box.diag() for box in B.boxes]
     finally:
         B.close()
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t1
     rel = [abs(d["free_energy"] - s["free_energy"]) / abs(s["free_energy"]) for d, s in zip(diags, single)]
-    return dict(S=S, boxes=len(specs), tol=tol_fp32, time_single=t_single, time_batch=t_batch,
-                speedup=t_single / max(t_batch, 1e-9), steps_single=[s["steps_fp32"] for s in single],
-                steps_batch=int(steps), resid_batch=[float(r) for r in resid],
-                resid_single=[s["resid"] for s in single], free_energy_rel_max=max(rel),
+    return dict(S=S, boxes=len(specs), tol=tol, precision="f64" if precision == LC_FP64 else "f32",
+                time_single=t_single, time_batch=t_batch, speedup=t_single / max(t_batch, 1e-9),
+                steps_single=[s["steps"] for s in single], steps_batch=int(steps),
+                resid_single=[s["resid"] for s in single], resid_batch=[float(r) for r in resid],
+                free_energy_rel_max=max(rel),
                 defects_equal=all(d["n_defect"] == s["n_defect"] for d, s in zip(diags, single)))
 
 
@@ -238,12 +263,23 @@ def main(argv=None):
     ap.add_argument("--big", action="store_true", help="also compare at 2S: R = 12, p = 32")
     ap.add_argument("--big-tol64", type=float, default=None, help="FP64 tolerance of the 2S case (default: FP32 only)")
     ap.add_argument("--big-mode", default="direct", choices=("direct", "upsample", "both"))
-    ap.add_argument("--batch-compare", type=int, default=0, help="also relax this many held-out boxes one by one "
-                    "and as one batch")
+    ap.add_argument("--batch-compare", type=int, default=0, help="also relax this many boxes one by one and as one "
+                    "batch (FP64, residual 1e-8)")
+    ap.add_argument("--batch-S", type=int, default=32, help="box size of the batched comparison")
+    ap.add_argument("--max-steps", type=int, default=2_000_000, help="step limit of each relaxation")
+    ap.add_argument("--only-batch", action="store_true", help="run the batched comparison only")
+    ap.add_argument("--any-pitch", action="store_true", help="also pitches whose Q period does not divide S (the "
+                    "periodic box then frustrates the helix, which relaxes by slowly changing its pitch)")
     ap.add_argument("--seed", type=int, default=1000)
     a = ap.parse_args(argv)
+    if a.only_batch:
+        res = dict(batched=batched_vs_single(commensurate_geometries(a.batch_compare or 16, a.batch_S, a.seed + 1),
+                                             a.batch_S, torch, max_steps=a.max_steps,
+                                             log=lambda m: print(m, flush=True)))
+        print(json.dumps(res, default=float), flush=True)
+        return res
     t0 = time.perf_counter()
-    specs = geometries(a.train + a.hold, a.S, a.seed)
+    specs = (geometries if a.any_pitch else commensurate_geometries)(a.train + a.hold, a.S, a.seed)
     data = relaxed_dataset(specs, a.S, a.relax_steps, torch)
     t_data = time.perf_counter() - t0
     print(f"dataset: {len(data)} relaxed boxes in {t_data:.1f} s", flush=True)
@@ -267,12 +303,13 @@ def main(argv=None):
     plain_of = {}
     for sp, S, tol64, mode in todo:
         key = (json.dumps(sp, sort_keys=True), S)
-        res["cases"].append(compare(net, sp, S, torch, a.tol32, tol64, mode=mode, plain=plain_of.get(key)))
+        res["cases"].append(compare(net, sp, S, torch, a.tol32, tol64, a.max_steps, mode=mode, plain=plain_of.get(key)))
         plain_of[key] = res["cases"][-1]["plain"]
         print(json.dumps(dict(case=res["cases"][-1]), default=float), flush=True)
     if a.batch_compare:
-        held = specs[a.train:a.train + a.batch_compare]
-        res["batched"] = batched_vs_single(held, a.S, torch, a.tol32)
+        res["batched"] = batched_vs_single(commensurate_geometries(a.batch_compare, a.batch_S, a.seed + 1), a.batch_S,
+                                           torch,
+                                           max_steps=a.max_steps)
         print(json.dumps(dict(batched=res["batched"]), default=float), flush=True)
     print(json.dumps(res, default=float), flush=True)
     return res
