@@ -172,6 +172,35 @@ int lc_lb_get_colloid(lc_lb* h, int id, double out[27]);
  * most cap entries; *n_out receives the total count. */
 int lc_lb_get_links(lc_lb* h, int32_t* node, int8_t* dir, int16_t* colloid, size_t cap, size_t* n_out);
 
+/* Defect analytics (Sec. 3.1: defects are where the order parameter is below
+ * 0.435; Sec. 3.2: the disclination loops around a colloid in a cholesteric).
+ * A defect node is a fluid node whose scalar order 3/2 lambda_max(Q), taken
+ * in FP64 from the stored Q, is below thr (> 0; the paper's value is 0.435).
+ * Components are the connected sets of defect nodes under face adjacency,
+ * periodic in x and y, and in z unless the box has walls; each is named by
+ * its smallest node index x + nx (y + ny z) ("root") and listed in root
+ * order.  Per component: the node count; the centroid [x, y, z], per
+ * periodic axis the circular mean (angle of the mean of exp(2 pi i x / L),
+ * times L / 2 pi, moved into [0, L)), along a walled z axis the plain mean;
+ * the gyration tensor (xx, xy, xz, yy, yz, zz), the mean of d d^T over the
+ * component, d the minimum-image displacement from the centroid.
+ * Writes at most cap components into the caller's host arrays (any may be
+ * NULL: root, size cap entries; centroid 3 cap, gyration 6 cap doubles);
+ * *n_defect and *n_comp receive the totals (either may be NULL).  Labels
+ * and counts are exact; the FP64 sums are accumulated in an unspecified
+ * order.  Device memory: 3 N + N/256 + 2 ints kept by the handle, plus
+ * 64 bytes per component during the call.  Synchronises the stream.
+ * LC_ERR_ARG for a threshold that is not positive and finite;
+ * LC_ERR_TIMEOUT if a bounded device loop gave up (not expected). */
+int lc_lb_defects(lc_lb* h, double thr, size_t cap, long long* n_defect, long long* n_comp, long long* root,
+                  long long* size, double* centroid, double* gyration);
+
+/* Per-node component labels of lc_lb_defects: labels[i] = root of node i's
+ * component, or -1 for a node that is not a defect node (solid nodes
+ * included); n >= N entries, host memory unless dst_is_device.
+ * Synchronises the stream. */
+int lc_lb_defect_labels(lc_lb* h, double thr, int32_t* labels, size_t n, int dst_is_device);
+
 int lc_lb_diagnostics(lc_lb* h, lc_diag* out);
 
 /* Allocation-free diagnostics: the paper has no counterpart; this exists for

@@ -128,6 +128,9 @@ def lib(use_torch_allocator: bool = True):
         L.lc_lb_get_colloid.argtypes = [vp, C.c_int, dp]
         L.lc_lb_get_links.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int8), C.POINTER(C.c_int16),
                                       C.c_size_t, C.POINTER(C.c_size_t)]
+        lp = C.POINTER(C.c_longlong)
+        L.lc_lb_defects.argtypes = [vp, C.c_double, C.c_size_t, lp, lp, lp, lp, dp, dp]
+        L.lc_lb_defect_labels.argtypes = [vp, C.c_double, vp, C.c_size_t, C.c_int]
         L.lc_lb_diagnostics.argtypes = [vp, C.POINTER(lc_diag)]
         L.lc_lb_diagnostics_noalloc.argtypes = [vp, C.POINTER(lc_diag)]
         L.lc_lb_profile.argtypes = [vp, C.c_int, dp]
@@ -327,6 +330,31 @@ class Solver:
                                            d.ctypes.data_as(C.POINTER(C.c_int8)),
                                            c.ctypes.data_as(C.POINTER(C.c_int16)), k, C.byref(n)))
         return node, d, c
+
+    def defects(self, thr=0.435) -> dict:
+        """Components of the defect nodes (lc_lb_defects): counts, roots,
+        sizes, centroids [n, 3] and gyration tensors [n, 6]."""
+        nd, nc = C.c_longlong(), C.c_longlong()
+        self._check(self.L.lc_lb_defects(self.h, float(thr), 0, C.byref(nd), C.byref(nc), None, None, None, None))
+        k = nc.value
+        root = np.empty(k, np.int64)
+        size = np.empty(k, np.int64)
+        cen = np.empty((k, 3))
+        gyr = np.empty((k, 6))
+        lp = C.POINTER(C.c_longlong)
+        self._check(self.L.lc_lb_defects(self.h, float(thr), k, C.byref(nd), C.byref(nc), root.ctypes.data_as(lp),
+                                         size.ctypes.data_as(lp), _dp(cen), _dp(gyr)))
+        return dict(n_defect=nd.value, n_comp=nc.value, root=root, size=size, centroid=cen, gyration=gyr)
+
+    def defect_labels(self, thr=0.435, out=None):
+        """Per-node root of the node's defect component, -1 elsewhere
+        (lc_lb_defect_labels); into a device int32 tensor when given."""
+        if out is not None and hasattr(out, "data_ptr"):
+            self._check(self.L.lc_lb_defect_labels(self.h, float(thr), C.c_void_p(out.data_ptr()), out.numel(), 1))
+            return out
+        a = np.empty(self.shape, np.int32)
+        self._check(self.L.lc_lb_defect_labels(self.h, float(thr), a.ctypes.data_as(C.c_void_p), a.size, 0))
+        return a
 
     # -- dynamics --------------------------------------------------------
     def step(self, n=1):

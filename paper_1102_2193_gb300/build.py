@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["lclb_kernels.cu", "lclb_api.cu", "lcnn_kernels.cu"]
+SOURCES = ["lclb_kernels.cu", "lclb_api.cu", "lclb_defects.cu", "lcnn_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-Xcompiler", "-ffp-contract=off",

@@ -94,6 +94,8 @@ struct lc_lb {
   DevBox hb{};                          // host copy of the device descriptor
   std::vector<DevColloid> col;          // host-side configuration of the colloids
   int nlinks = 0;
+  int* def = nullptr;                   // defect analytics: parent, comp, list (N each), block counts, total, error
+  size_t def_cap = 0;
   std::string err;
 };
 
@@ -1283,6 +1285,96 @@ int lc_lb_get_links(lc_lb* h, int32_t* node, int8_t* dir, int16_t* colloid, size
     if (dir) dir[i] = dr[ord[i]];
     if (colloid) colloid[i] = c8[ord[i]];
   }
+  return LC_OK;
+}
+
+// Labels the defect nodes of box h (see lc_lb_defects): parent[i] = the
+// smallest node index of i's component, or -1, in h->def; the components
+// numbered in root order.  *ncomp receives their number.
+static int defects_label(lc_lb* h, double thr, int* ncomp) {
+  if (!(thr > 0.0) || !std::isfinite(thr)) return fail(&h->err, LC_ERR_ARG, "defect threshold must be positive");
+  Group* g = h->g;
+  const int N = h->hb.N;
+  const int nb = defect_blocks(N);
+  const size_t need = (size_t)3 * N + nb + 2;
+  if (h->def_cap < need) {
+    if (h->def) g->mem.put(h->def, g->al);
+    h->def = (int*)galloc(g, sizeof(int) * need);
+    h->def_cap = h->def ? need : 0;
+    if (!h->def) return fail(&h->err, LC_ERR_OOM, "defect label allocation failed");
+  }
+  int* parent = h->def;
+  int* comp = parent + N;
+  int* list = comp + N;
+  int* blockcnt = list + N;
+  int* total = blockcnt + nb;
+  int* errf = total + 1;
+  CK(cudaMemsetAsync(errf, 0, sizeof(int), g->stream), &h->err);
+  CK(launch_defects_label(g->prec, g->d_boxes, h->index, N, thr, parent, comp, list, blockcnt, total, errf, g->stream),
+     &h->err);
+  int hv[2] = {0, 0};
+  CK(cudaMemcpyAsync(hv, total, sizeof(hv), cudaMemcpyDeviceToHost, g->stream), &h->err);
+  CK(cudaStreamSynchronize(g->stream), &h->err);
+  if (hv[1]) return fail(&h->err, LC_ERR_TIMEOUT, "defect labelling: a bounded find/union loop gave up");
+  *ncomp = hv[0];
+  return LC_OK;
+}
+
+int lc_lb_defects(lc_lb* h, double thr, size_t cap, long long* n_defect, long long* n_comp, long long* root,
+                  long long* size, double* centroid, double* gyration) {
+  if (int rc = h_check(h)) return rc;
+  int nc = 0;
+  if (int rc = defects_label(h, thr, &nc)) return rc;
+  Group* g = h->g;
+  const int N = h->hb.N;
+  std::vector<int> hl((size_t)nc), hs((size_t)nc);
+  std::vector<double> hc((size_t)3 * nc), hg((size_t)6 * nc);
+  if (nc > 0) {
+    const size_t ib = ((sizeof(int) * (size_t)nc + 15) / 16) * 16;
+    char* tmp = (char*)galloc(g, ib + sizeof(double) * 15 * (size_t)nc);
+    if (!tmp) return fail(&h->err, LC_ERR_OOM, "defect statistics allocation failed");
+    int* dsz = (int*)tmp;
+    double* circ = (double*)(tmp + ib);
+    double* cen = circ + 6 * (size_t)nc;
+    double* gyr = cen + 3 * (size_t)nc;
+    int rc = LC_OK;
+    if (cudaMemsetAsync(tmp, 0, ib + sizeof(double) * 15 * (size_t)nc, g->stream) != cudaSuccess ||
+        launch_defects_stats(g->d_boxes, h->index, N, nc, h->def, h->def + N, dsz, circ, cen, gyr, g->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(hl.data(), h->def + 2 * (size_t)N, sizeof(int) * nc, cudaMemcpyDeviceToHost, g->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(hs.data(), dsz, sizeof(int) * nc, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+        cudaMemcpyAsync(hc.data(), cen, sizeof(double) * 3 * nc, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+        cudaMemcpyAsync(hg.data(), gyr, sizeof(double) * 6 * nc, cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+        cudaStreamSynchronize(g->stream) != cudaSuccess)
+      rc = fail(&h->err, LC_ERR_CUDA, "defect statistics: %s", cudaGetErrorString(cudaGetLastError()));
+    g->mem.put(tmp, g->al);
+    if (rc) return rc;
+  }
+  long long nd = 0;
+  for (int v : hs) nd += v;
+  if (n_defect) *n_defect = nd;
+  if (n_comp) *n_comp = nc;
+  const size_t k = std::min(cap, (size_t)nc);
+  for (size_t c = 0; c < k; ++c) {
+    if (root) root[c] = hl[c];
+    if (size) size[c] = hs[c];
+    for (int a = 0; a < 3 && centroid; ++a) centroid[3 * c + a] = hc[3 * c + a];
+    for (int a = 0; a < 6 && gyration; ++a) gyration[6 * c + a] = hg[6 * c + a];
+  }
+  return LC_OK;
+}
+
+int lc_lb_defect_labels(lc_lb* h, double thr, int32_t* labels, size_t n, int dst_is_device) {
+  if (int rc = h_check(h)) return rc;
+  if (!labels || n < (size_t)h->hb.N) return fail(&h->err, LC_ERR_ARG, "labels needs N = %d entries", h->hb.N);
+  int nc = 0;
+  if (int rc = defects_label(h, thr, &nc)) return rc;
+  Group* g = h->g;
+  CK(cudaMemcpyAsync(labels, h->def, sizeof(int32_t) * h->hb.N,
+                     dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream),
+     &h->err);
+  CK(cudaStreamSynchronize(g->stream), &h->err);
   return LC_OK;
 }
 

@@ -49,4 +49,16 @@ int diag_state_blocks(int N);
 cudaError_t launch_diag_state(int prec, const DevBox* boxes, int b, int N, double* part, cudaStream_t s);
 cudaError_t launch_reduce(const double* part, int rec0, int n, int w, unsigned maxmask, double* out, cudaStream_t s);
 
+// Defect analytics of box b (lclb_defects.cu).  Labelling: parent[i] = the
+// smallest node index of i's component of defect nodes, or -1; comp[root] =
+// the component's rank in root order, list[rank] = root; blockcnt holds
+// defect_blocks(N) ints; *total = number of components; *err set when a
+// bounded loop gave up.  Statistics: size (ncomp ints), circ (6 ncomp),
+// cen (3 ncomp), gyr (6 ncomp) doubles, size/circ/gyr zeroed by the caller.
+int defect_blocks(int N);
+cudaError_t launch_defects_label(int prec, const DevBox* boxes, int b, int N, double thr, int* parent, int* comp,
+                                 int* list, int* blockcnt, int* total, int* err, cudaStream_t s);
+cudaError_t launch_defects_stats(const DevBox* boxes, int b, int N, int ncomp, const int* parent, const int* comp,
+                                 int* size, double* circ, double* cen, double* gyr, cudaStream_t s);
+
 }  // namespace lclb

@@ -115,3 +115,23 @@ def batched_sweep(seed: int = 4, n: int = 64) -> list:
                         init=dict(kind="helix" if chol else "uniaxial", axis=2, n=(0, 0, 1), amp=1e-3,
                                   seed=seed * 1000 + len(out))))
     return out
+
+
+def uniaxial_field(order, director) -> np.ndarray:
+    """5-component Q ``[5][z][y][x]`` of a uniaxial field with scalar order
+    ``order[z][y][x]`` and unit director ``director[3][z][y][x]``:
+    Q = S (n n - I/3), stored as (xx, xy, xz, yy, yz)."""
+    S = np.asarray(order, dtype=np.float64)
+    n = np.asarray(director, dtype=np.float64)
+    return np.stack([S * (n[0] * n[0] - 1.0 / 3.0), S * n[0] * n[1], S * n[0] * n[2],
+                     S * (n[1] * n[1] - 1.0 / 3.0), S * n[1] * n[2]])
+
+
+def defect_field(shape, seed: int, lo: float = 0.35, hi: float = 0.75) -> np.ndarray:
+    """Seeded uniaxial Q with random directors and, per node, a scalar order
+    drawn from U[lo, hi): with the paper's threshold 0.435 about a fifth of
+    the nodes are defect nodes, scattered in clusters of many shapes."""
+    rng = np.random.default_rng(seed)
+    n = rng.normal(size=(3, *shape))
+    n /= np.linalg.norm(n, axis=0)
+    return uniaxial_field(rng.uniform(lo, hi, size=shape), n)

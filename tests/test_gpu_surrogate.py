@@ -202,14 +202,18 @@ def test_warm_start_pipeline_small(P):
 def test_trained_network_starts_closer_than_helix(P):
     """What the trained network gains over the method without it: on held-out
     geometries its proposal is closer to the relaxed state (masked MSE over
-    fluid nodes) than the helix start that the plain relaxation begins from."""
+    fluid nodes) than the helix start that the plain relaxation begins from.
+    32^3 boxes with pitches whose Q period divides the box (the periodic box
+    then holds the helix without a twist wall), 24 for training, 4 held out
+    (at 64^3 with 96 training boxes the proposal is 7x closer; with this
+    small set, 1.6x)."""
     from paper_1102_2193_gb300 import warmstart as ws
     from paper_1102_2193_gb300.surrogate import UNet
-    S = 16
-    specs = ws.geometries(10, S, seed=7)
-    data = ws.relaxed_dataset(specs, S, 2000, torch)
+    S = 32
+    specs = ws.commensurate_geometries(28, S, seed=7)
+    data = ws.relaxed_dataset(specs, S, 6000, torch)
     net = UNet(S=S, seed=4)
-    ws.train(net, data[:8], epochs=30, lr=3e-3)
-    l_net = ws.evaluate_loss(net, data[8:])
-    l_helix = ws.evaluate_loss(UNet(S=S, seed=4), data[8:])  # untrained: head output 0, i.e. the helix start
-    assert l_net < l_helix, (l_net, l_helix)
+    ws.train(net, data[:24], epochs=25, lr=2e-3)
+    l_net = ws.evaluate_loss(net, data[24:])
+    l_helix = ws.evaluate_loss(UNet(S=S, seed=4), data[24:])  # untrained: head output 0, i.e. the helix start
+    assert l_net < 0.8 * l_helix, (l_net, l_helix)  # measured 0.62 on a GB300
