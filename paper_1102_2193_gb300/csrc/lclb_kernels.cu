@@ -406,26 +406,62 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * 
 }
 
 // ---------------------------------------------------------------------------
+// x-neighbour values from the adjacent lanes
+// ---------------------------------------------------------------------------
+// The lanes of a warp hold consecutive x of one row, so the K values of the
+// x +- 1 neighbours of a node come from lanes +- 1 by shuffles; a lane whose
+// neighbour is not held by the adjacent lane (the tile's edge lanes, the
+// periodic wrap, the end of a ragged row) loads it.  All 32 lanes call this.
+// xn[0] = x + 1, xn[1] = x - 1 (the order of face_neighbours).
+template <typename T, int K>
+__device__ __forceinline__ void x_neighbours(const T* __restrict__ F, size_t N, const T self[K], int lane, int x,
+                                             int nx, int row, bool valid, T xn[2][K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    xn[0][k] = __shfl_down_sync(0xffffffffu, self[k], 1);
+    xn[1][k] = __shfl_up_sync(0xffffffffu, self[k], 1);
+  }
+  if (!valid) return;
+  if (lane == TX - 1 || x + 1 >= nx) {
+    const int j = (x + 1 == nx ? 0 : x + 1) + row;
+#pragma unroll
+    for (int k = 0; k < K; ++k) xn[0][k] = ldg(F + (size_t)k * N + j);
+  }
+  if (lane == 0) {
+    const int j = (x == 0 ? nx - 1 : x - 1) + row;
+#pragma unroll
+    for (int k = 0; k < K; ++k) xn[1][k] = ldg(F + (size_t)k * N + j);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // stored-stress variant: k_stress stores H and P once per fluid node, k_lbp
 // takes the body force from the stored P
 // ---------------------------------------------------------------------------
 // Node i of the stored-stress kernel: gather (surface values at solid or wall
 // faces when near), H, P, stores, and for near nodes the colloid LC force.
+// A plain node (NEAR_NODE false) takes its own Q and that of its x-neighbours
+// from pq (self, x + 1, x - 1; gathered by the warp) and loads the rest.
 template <typename T, bool NEAR_NODE>
 __device__ __forceinline__ void stress_node(const DevBox& B, const PhysT<T>& PP, const T* __restrict__ Q,
                                             T* __restrict__ Hb, T* __restrict__ Pb, int x, int y, int z, int i,
-                                            uint8_t m, int mode, int& my_c, double my_acc[6]) {
+                                            uint8_t m, int mode, int& my_c, double my_acc[6],
+                                            const T (*pq)[5] = nullptr) {
   const int N = B.N;
   T qi[5], qn[6][5], h[5], p[9], fp;
   if (NEAR_NODE) {
     gather_q(B, Q, x, y, z, i, m, qi, qn, nullptr);
   } else {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) qi[k] = ldg(Q + (size_t)k * N + i);
     int nb[6], zz[2];
     face_neighbours(B, x, y, z, nb, zz);
 #pragma unroll
-    for (int d = 0; d < 6; ++d)
+    for (int k = 0; k < 5; ++k) {
+      qi[k] = pq[0][k];
+      qn[0][k] = pq[1][k];
+      qn[1][k] = pq[2][k];
+    }
+#pragma unroll
+    for (int d = 2; d < 6; ++d)
 #pragma unroll
       for (int k = 0; k < 5; ++k) qn[d][k] = ldg(Q + (size_t)k * N + nb[d]);
   }
@@ -483,7 +519,11 @@ __global__ void __launch_bounds__(TX * TY) k_stress(const DevBox* __restrict__ b
       const uint8_t m = valid ? B.mask[i] : (uint8_t)1;
       const bool fluid = (m & IDMASK) == 0;
       const bool near = fluid && (m & NEAR);
-      if (fluid && !near) stress_node<T, false>(B, PP, Q, Hb, Pb, x, y, z, i, m, mode, my_c, my_acc);
+      T pq[3][5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) pq[0][k] = valid ? ldg(Q + (size_t)k * B.N + i) : T(0);
+      x_neighbours<T, 5>(Q, (size_t)B.N, pq[0], lane, x, nx, nx * (y + ny * z), valid, &pq[1]);
+      if (fluid && !near) stress_node<T, false>(B, PP, Q, Hb, Pb, x, y, z, i, m, mode, my_c, my_acc, pq);
       const unsigned nb = __ballot_sync(0xffffffffu, near);
       if (nb) {
         if (near) sq[wy][nq + __popc(nb & ((1u << lane) - 1u))] = i;
@@ -725,10 +765,13 @@ __global__ void __launch_bounds__(32 * (BY + 3), (sizeof(T) == 4 && BY <= 4) ? 2
 // velocity gradient, upwind advective fluxes through the faces (zero across
 // solid or wall faces, which only near nodes have), H stored by the stress
 // kernel of this step; Q^{n+1} stored, residual folded into (rsum, rmax).
+// A plain node (NEAR_NODE false) takes its own Q and u and those of its
+// x-neighbours from pq and pu (self, x + 1, x - 1; gathered by the warp).
 template <typename T, bool NEAR_NODE>
 __device__ __forceinline__ void lc_update_node(const DevBox& B, const PhysT<T>& PP, const T* __restrict__ Q,
                                                T* __restrict__ Qo, const T* __restrict__ U, int x, int y, int z,
-                                               int i, uint8_t m, T& rsum, T& rmax) {
+                                               int i, uint8_t m, T& rsum, T& rmax, const T (*pq)[5] = nullptr,
+                                               const T (*pu)[3] = nullptr) {
   const int N = B.N;
   const T Gam = PP.Gamma, xi = PP.xi;
   // H of this node was stored by the stress kernel of this step; Q of the
@@ -738,7 +781,7 @@ __device__ __forceinline__ void lc_update_node(const DevBox& B, const PhysT<T>& 
   T qi[5], qn[6][5], h[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    qi[c] = ldg(Q + (size_t)c * N + i);
+    qi[c] = NEAR_NODE ? ldg(Q + (size_t)c * N + i) : pq[0][c];
     h[c] = Hb[(size_t)c * N + i];
   }
   int nb[6], zz[2];
@@ -746,11 +789,18 @@ __device__ __forceinline__ void lc_update_node(const DevBox& B, const PhysT<T>& 
   T ui[3], un[6][3];
   bool fl[6];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) ui[a] = ldg(U + (size_t)a * N + i);
+  for (int a = 0; a < 3; ++a) ui[a] = NEAR_NODE ? ldg(U + (size_t)a * N + i) : pu[0][a];
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     const int j = nb[d];
     fl[d] = !NEAR_NODE || (j >= 0 && (B.mask[j] & IDMASK) == 0);
+    if (!NEAR_NODE && d < 2) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) un[d][a] = pu[1 + d][a];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) qn[d][c] = pq[1 + d][c];
+      continue;
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) un[d][a] = (!NEAR_NODE || j >= 0) ? ldg(U + (size_t)a * N + j) : T(0);
 #pragma unroll
@@ -827,8 +877,9 @@ __device__ __forceinline__ void lc_update_node(const DevBox& B, const PhysT<T>& 
 // k_lc: Beris-Edwards update; plain nodes of a warp's row together, nodes
 // next to a solid or wall queued and updated 32 at a time.
 template <typename T, int TY>
-__global__ void __launch_bounds__(TX * TY) k_lc(const DevBox* __restrict__ boxes, const int4* __restrict__ tiles,
-                                                int ntiles, int zc, int mode, double* __restrict__ part) {
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 640 : 256) / (TX * TY)) k_lc(
+    const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
+    double* __restrict__ part) {
   __shared__ DevBox B;
   __shared__ double sred[32 * 2];
   __shared__ int sq[TY][2 * TX];
@@ -855,7 +906,15 @@ __global__ void __launch_bounds__(TX * TY) k_lc(const DevBox* __restrict__ boxes
       const uint8_t m = valid ? B.mask[i] : (uint8_t)1;
       const bool fluid = (m & IDMASK) == 0;
       const bool near = fluid && (m & NEAR);
-      if (fluid && !near) lc_update_node<T, false>(B, PP, Q, Qo, U, x, y, z, i, m, rsum, rmax);
+      T pq[3][5], pu[3][3];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) pq[0][k] = valid ? ldg(Q + (size_t)k * B.N + i) : T(0);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) pu[0][a] = valid ? ldg(U + (size_t)a * B.N + i) : T(0);
+      const int row = nx * (y + ny * z);
+      x_neighbours<T, 5>(Q, (size_t)B.N, pq[0], lane, x, nx, row, valid, &pq[1]);
+      x_neighbours<T, 3>(U, (size_t)B.N, pu[0], lane, x, nx, row, valid, &pu[1]);
+      if (fluid && !near) lc_update_node<T, false>(B, PP, Q, Qo, U, x, y, z, i, m, rsum, rmax, pq, pu);
       const unsigned nb = __ballot_sync(0xffffffffu, near);
       if (nb) {
         if (near) sq[wy][nq + __popc(nb & ((1u << lane) - 1u))] = i;
