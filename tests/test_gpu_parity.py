@@ -217,6 +217,31 @@ def test_moving_colloid_rediscretisation(P, prec):
     assert (ng == no).all() and (dg == do).all() and (cg == co).all()
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_two_mobile_colloids_approaching(P, prec):
+    """Two mobile colloids (strong normal and weak planar anchoring) launched
+    towards each other in a cholesteric: both re-discretise in the same steps
+    and the LC stress between them (the defect-mediated interaction) enters
+    each colloid's update; GPU against oracle, links bit-exact."""
+    L = (28, 22, 20)
+    prm = dict(synth.NEMATIC, q0=2 * math.pi / 20)
+    cols = [dict(X=(8.3, 10.6, 9.2), a0=3.5, anchoring=0, w=float("inf"), mobile=True),
+            dict(X=(19.1, 10.9, 9.9), a0=3.0, anchoring=1, w=0.02, mobile=True)]
+    g, o = make_pair(P, L, prm, P.LC_FP32 if prec == "f32" else P.LC_FP64, colloids=cols,
+                     init=("helix", 2, 1e-2, 5))
+    for s in (g, o):
+        s.set_colloid_velocity(0, (0.02, 0.0, 0.003))
+        s.set_colloid_velocity(1, (-0.02, 0.002, 0.0))
+    s0 = o.get_solid()
+    g.step(100)
+    o.step(100)
+    assert (o.get_solid() != s0).any()
+    compare(g, o, TOL32 if prec == "f32" else TOL64, ncol=2, radii=[3.5, 3.0])
+    ng, dg, cg = g.links()
+    no, do, co = o.links()
+    assert (ng == no).all() and (dg == do).all() and (cg == co).all()
+
+
 def test_lc_off_and_flow_off_switches(P):
     L = (20, 16, 12)
     for lc, flow in ((False, True), (True, False)):
