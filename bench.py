@@ -192,8 +192,14 @@ def cpu_baseline(w, budget_s: float) -> dict:
         dt = time.perf_counter() - t0
         if dt >= budget_s or n >= 1000:
             break
+    # the same oracle on one thread, one further step (the scaling of the host baseline)
+    o.set_threads(1)
+    t1 = time.perf_counter()
+    o.step(1)
+    dt1 = time.perf_counter() - t1
     return dict(value=nx * ny * nz * n / dt / 1e6, unit="MLUPS", cores=cores, kind="oracle",
-                sample=f"{n} steps of the {nx}x{ny}x{nz} workload after 1 untimed step, FP64, {cores} threads")
+                sample=f"{n} steps of the {nx}x{ny}x{nz} workload after 1 untimed step, FP64, {cores} threads",
+                value_1_thread=nx * ny * nz / dt1 / 1e6, sample_1_thread="1 further step on 1 thread")
 
 
 def run_reference(args, ws, rank):
