@@ -434,14 +434,54 @@ __device__ __forceinline__ void x_neighbours(const T* __restrict__ F, size_t N, 
   }
 }
 
+// Values of the thread's own column (x, y) down the z march: at the start of
+// a tile, z0 - 1 and z0 (the plane below z0 wraps in a periodic box; beyond a
+// wall the value is 0 and unused, such nodes being near nodes).  Each step
+// loads z + 1 into pc[3], takes z into pc[0] and z - 1 into pc[4]
+// (pc[1], pc[2] are the x-neighbours), and column_roll moves the window up.
+template <typename T, int K>
+__device__ __forceinline__ void column_start(const DevBox& B, const T* __restrict__ F, int x, int y, int z0,
+                                             bool valid, T cz[2][K]) {
+  const int zm = z0 > 0 ? z0 - 1 : (B.wall_z ? -1 : B.nz - 1);
+  const size_t N = (size_t)B.N;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    cz[0][k] = (valid && zm >= 0) ? ldg(F + (size_t)k * N + x + B.nx * (y + B.ny * zm)) : T(0);
+    cz[1][k] = valid ? ldg(F + (size_t)k * N + x + B.nx * (y + B.ny * z0)) : T(0);
+  }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void column_next(const DevBox& B, const T* __restrict__ F, int x, int y, int z, bool valid,
+                                            const T cz[2][K], T pc[5][K]) {
+  const int zp = z + 1 < B.nz ? z + 1 : (B.wall_z ? -1 : 0);
+  const size_t N = (size_t)B.N;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    pc[0][k] = cz[1][k];
+    pc[4][k] = cz[0][k];
+    pc[3][k] = (valid && zp >= 0) ? ldg(F + (size_t)k * N + x + B.nx * (y + B.ny * zp)) : T(0);
+  }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void column_roll(T cz[2][K], const T pc[5][K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    cz[0][k] = pc[0][k];
+    cz[1][k] = pc[3][k];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // stored-stress variant: k_stress stores H and P once per fluid node, k_lbp
 // takes the body force from the stored P
 // ---------------------------------------------------------------------------
 // Node i of the stored-stress kernel: gather (surface values at solid or wall
 // faces when near), H, P, stores, and for near nodes the colloid LC force.
-// A plain node (NEAR_NODE false) takes its own Q and that of its x-neighbours
-// from pq (self, x + 1, x - 1; gathered by the warp) and loads the rest.
+// A plain node (NEAR_NODE false) takes its own Q and that of its x- and
+// z-neighbours from pq (self, x + 1, x - 1, z + 1, z - 1: gathered by the warp
+// and rolled down the thread's column) and loads the y-neighbours.
 template <typename T, bool NEAR_NODE>
 __device__ __forceinline__ void stress_node(const DevBox& B, const PhysT<T>& PP, const T* __restrict__ Q,
                                             T* __restrict__ Hb, T* __restrict__ Pb, int x, int y, int z, int i,
@@ -459,9 +499,11 @@ __device__ __forceinline__ void stress_node(const DevBox& B, const PhysT<T>& PP,
       qi[k] = pq[0][k];
       qn[0][k] = pq[1][k];
       qn[1][k] = pq[2][k];
+      qn[4][k] = pq[3][k];
+      qn[5][k] = pq[4][k];
     }
 #pragma unroll
-    for (int d = 2; d < 6; ++d)
+    for (int d = 2; d < 4; ++d)
 #pragma unroll
       for (int k = 0; k < 5; ++k) qn[d][k] = ldg(Q + (size_t)k * N + nb[d]);
   }
@@ -514,14 +556,15 @@ __global__ void __launch_bounds__(TX * TY) k_stress(const DevBox* __restrict__ b
     int my_c = -1;
     double my_acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     int nq = 0;  // queued near nodes of this warp (warp-uniform)
+    T qz[2][5];  // Q of the thread's own column at z - 1 and z, rolled down the z march
+    column_start<T, 5>(B, Q, x, y, td.w, valid, qz);
     for (int z = td.w; z < zend; ++z) {
       const int i = x + nx * (y + ny * z);
       const uint8_t m = valid ? B.mask[i] : (uint8_t)1;
       const bool fluid = (m & IDMASK) == 0;
       const bool near = fluid && (m & NEAR);
-      T pq[3][5];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) pq[0][k] = valid ? ldg(Q + (size_t)k * B.N + i) : T(0);
+      T pq[5][5];
+      column_next<T, 5>(B, Q, x, y, z, valid, qz, pq);
       x_neighbours<T, 5>(Q, (size_t)B.N, pq[0], lane, x, nx, nx * (y + ny * z), valid, &pq[1]);
       if (fluid && !near) stress_node<T, false>(B, PP, Q, Hb, Pb, x, y, z, i, m, mode, my_c, my_acc, pq);
       const unsigned nb = __ballot_sync(0xffffffffu, near);
@@ -539,6 +582,7 @@ __global__ void __launch_bounds__(TX * TY) k_stress(const DevBox* __restrict__ b
           __syncwarp();
         }
       }
+      column_roll<T, 5>(qz, pq);
     }
     if (lane < nq) {
       const int j = sq[wy][lane];
@@ -767,6 +811,9 @@ __global__ void __launch_bounds__(32 * (BY + 3), (sizeof(T) == 4 && BY <= 4) ? 2
 // kernel of this step; Q^{n+1} stored, residual folded into (rsum, rmax).
 // A plain node (NEAR_NODE false) takes its own Q and u and those of its
 // x-neighbours from pq and pu (self, x + 1, x - 1; gathered by the warp).
+// Holding the z-neighbours in registers down the z march, as the stress
+// kernel does, pushed this kernel past its 96-register cap (spills, 76 us
+// against 71 us).
 template <typename T, bool NEAR_NODE>
 __device__ __forceinline__ void lc_update_node(const DevBox& B, const PhysT<T>& PP, const T* __restrict__ Q,
                                                T* __restrict__ Qo, const T* __restrict__ U, int x, int y, int z,
