@@ -45,6 +45,13 @@ def test_error_paths_without_device(so):
     # a null output pointer is rejected before any CUDA call
     assert lib.lc_lb_create(None, None, None, None) == -1
     assert lib.lc_lb_last_error(None)
+    # so is a null handle, for the defect analytics too
+    lib.lc_lb_defects.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_size_t] + [ctypes.c_void_p] * 6
+    lib.lc_lb_defect_labels.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t,
+                                        ctypes.c_int]
+    assert lib.lc_lb_defects(None, 0.435, 0, None, None, None, None, None, None) == -1
+    assert lib.lc_lb_defect_labels(None, 0.435, None, 0, 0) == -1
+    assert b"null handle" in lib.lc_lb_last_error(None)
 
 
 def test_binding_names_match_header():
