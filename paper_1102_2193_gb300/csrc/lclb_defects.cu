@@ -4,7 +4,8 @@
 // a threshold (0.435 in the paper, the isosurface level of its defect
 // renderings); the disclination loops of Sec. 3.2 (Saturn ring, figure of
 // eight) and the boojums of Sec. 3.1 are the connected sets of such nodes.
-//   k_def_init     defect test per node (FP64 from the stored Q), parent[i] = i or -1
+//   k_def_init     defect test per node (FP64 from the stored Q, by Sylvester's
+//                  criterion), parent[i] = i or -1
 //   k_def_union    union-find over the +x, +y, +z face links between defect nodes
 //                  (lock-free: a root is linked under the smaller root by CAS, so
 //                  the root of every set is its smallest node index)
@@ -26,19 +27,15 @@ namespace lclb {
 constexpr int DEF_ITER_MAX = 1 << 24;
 constexpr double DEF_TWO_PI = 6.283185307179586476925286766559;
 
-// Largest eigenvalue of the symmetric traceless Q (5-component storage),
-// closed-form trigonometric solution of the characteristic cubic (Smith,
-// CACM 1961).
-__device__ __forceinline__ double def_lambda_max(const double q[5]) {
-  const double a00 = q[0], a01 = q[1], a02 = q[2], a11 = q[3], a12 = q[4], a22 = -q[0] - q[3];
-  const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
-  const double p2 = a00 * a00 + a11 * a11 + a22 * a22 + 2.0 * p1;
-  if (!(p2 > 0.0)) return 0.0;
-  const double p = sqrt(p2 / 6.0);
-  const double b00 = a00 / p, b01 = a01 / p, b02 = a02 / p, b11 = a11 / p, b12 = a12 / p, b22 = a22 / p;
-  const double det = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
-  const double r = fmin(1.0, fmax(-1.0, det / 2.0));
-  return 2.0 * p * cos(acos(r) / 3.0);
+// Defect test 3/2 lambda_max(Q) < thr without the eigenvalue: with
+// t = thr / 1.5, every eigenvalue of the symmetric Q is below t exactly when
+// t I - Q is positive definite, i.e. (Sylvester's criterion) when its three
+// leading principal minors are positive.  FP64 multiply-adds only.
+__device__ __forceinline__ bool def_is_defect(const double q[5], double t) {
+  const double m00 = t - q[0], m11 = t - q[3], m22 = t + q[0] + q[3];
+  const double m01 = -q[1], m02 = -q[2], m12 = -q[4];
+  if (!(m00 > 0.0) || !(m00 * m11 - m01 * m01 > 0.0)) return false;
+  return m00 * (m11 * m22 - m12 * m12) - m01 * (m01 * m22 - m12 * m02) + m02 * (m01 * m12 - m11 * m02) > 0.0;
 }
 
 // Root of x.  parent values only ever point to smaller indices, so x
@@ -91,7 +88,7 @@ __global__ void __launch_bounds__(256) k_def_init(const DevBox* __restrict__ box
     double q[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) q[k] = (double)Q[(size_t)k * B.N + i];
-    if (1.5 * def_lambda_max(q) < thr) v = i;
+    if (def_is_defect(q, thr / 1.5)) v = i;
   }
   parent[i] = v;
 }
