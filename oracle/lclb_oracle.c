@@ -20,9 +20,13 @@
  *   - Central first differences and the 7-point Laplacian; first-order upwind
  *     advective fluxes at control-volume faces (Sec. 2.2, Fig. 1).
  *   - Q update: explicit Euler of Eq. 2 with the Beris-Edwards co-rotation term.
- *   - Colloid: explicit Euler ("molecular dynamics-like step", Sec. 2.2).
+ *   - Colloid: the "molecular dynamics-like step" of Sec. 2.2 taken implicit
+ *     in the velocity-dependent part of the link force (colloid_update).
  *
- * Parity status: every function below is pinned by a CPU test except the
+ * Parity status: every function below is pinned by a CPU test, including the
+ * surface value at colloid faces (homeotropic normal at the solid node,
+ * planar projection of the largest-eigenvalue director, tie-break) and the
+ * LC torque (symmetry and the discrete angular-momentum balance), except the
  * drag-anisotropy and cholesteric defect-topology outcomes, which no printed
  * number of the paper fixes (parity unpinned against the paper; the CUDA path
  * is compared with this oracle only).
