@@ -84,10 +84,9 @@ __global__ void __launch_bounds__(256) k_def_init(const DevBox* __restrict__ box
   if (i >= B.N) return;
   int v = -1;
   if ((B.mask[i] & IDMASK) == 0) {
-    const T* Q = static_cast<const T*>(B.Q[B.st->qpar]);
     double q[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) q[k] = (double)Q[(size_t)k * B.N + i];
+    for (int k = 0; k < 5; ++k) q[k] = load_q<T>(B, i, k);
     if (def_is_defect(q, thr / 1.5)) v = i;
   }
   parent[i] = v;

@@ -7,6 +7,7 @@
 // Q stores (xx, xy, xz, yy, yz); zz = -xx - yy.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace lclb {
@@ -81,6 +82,10 @@ struct DevBox {
   int* chg;             // change list: (node, colloid << 1 | uncovered) pairs
   void* f[2];
   void* Q[2];
+  // FP32 storage only (null for FP64): the BF16 remainder of each stored Q
+  // component, so that hi + lo carries the increments that rounding hi alone
+  // would drop (compensated storage; 5 comps, same layout as Q)
+  __nv_bfloat16* Qlo[2];
   void* u;
   void* F;
   void* H;              // molecular field of the current Q at fluid nodes (5 comps), written by the stress kernels
@@ -139,6 +144,36 @@ __device__ __forceinline__ bool inside_colloid(const DevBox& B, int x, int y, in
   return r2 < __dmul_rn(C.a0, C.a0);
 }
 
+// Compensated storage of Q in FP32: a value v (FP64) is kept as hi = RN32(v)
+// and lo = RNbf16(v - hi); the stored value is hi + lo.
+__device__ __forceinline__ void split_q(double v, float& hi, __nv_bfloat16& lo) {
+  hi = (float)v;
+  lo = __double2bfloat16(v - (double)hi);
+}
+
+// hi + lo + d carried into a new (hi, lo): the exact sum hi + s of
+// s = lo + d by Knuth's branch-free two-sum (hi' = RN(hi + s) and the exact
+// error of that addition), the error then rounded to BF16.
+__device__ __forceinline__ void add_compensated(float hi, float lo, float d, float& hi_out, __nv_bfloat16& lo_out) {
+  const float s = lo + d;
+  const float h = __fadd_rn(hi, s);
+  const float bb = __fsub_rn(h, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(h, bb)), __fsub_rn(s, bb));
+  hi_out = h;
+  lo_out = __float2bfloat16_rn(err);
+}
+
+// Stored value of component k of node i of the current Q (hi + lo for FP32).
+template <typename T>
+__device__ __forceinline__ double load_q(const DevBox& B, int i, int k) {
+  const int qpar = B.st->qpar;
+  const size_t o = (size_t)k * B.N + i;
+  if constexpr (sizeof(T) == 4)
+    return (double)static_cast<const float*>(B.Q[qpar])[o] + (double)__bfloat162float(B.Qlo[qpar][o]);
+  else
+    return static_cast<const double*>(B.Q[qpar])[o];
+}
+
 // Q entry (a,b) of the 5-component storage.
 template <typename T>
 __device__ __forceinline__ T qab(const T* q, int a, int b) {
@@ -185,6 +220,39 @@ __device__ __forceinline__ void rigid_velocity(const double* V, const double* W,
 // Principal eigenvector of a symmetric traceless 3x3 matrix (5-component
 // storage), from the closed-form trigonometric eigenvalue of a symmetric 3x3
 // matrix (Smith, CACM 1961) and a cross product of two rows of (A - l I).
+// FP64: the eigenvalue of the FP32 evaluation refined by two Newton steps on
+// the characteristic polynomial det(A - l I) = -l^3 + (Tr A^2 / 2) l + det A
+// (no FP64 transcendental functions), then the FP64 cross products.
+template <typename T>
+__device__ void principal_dir(const T* q, T n[3]);
+
+__device__ __forceinline__ double principal_lambda_f64(const double* q) {
+  const double a00 = q[0], a01 = q[1], a02 = q[2], a11 = q[3], a12 = q[4], a22 = -q[0] - q[3];
+  const float qf[5] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3], (float)q[4]};
+  // FP32 seed: the largest eigenvalue by the trigonometric formula
+  const float f00 = qf[0], f01 = qf[1], f02 = qf[2], f11 = qf[3], f12 = qf[4], f22 = -qf[0] - qf[3];
+  const float p1 = f01 * f01 + f02 * f02 + f12 * f12;
+  const float p2 = f00 * f00 + f11 * f11 + f22 * f22 + 2.f * p1;
+  float lam32 = 0.f;
+  if (p2 > 0.f) {
+    const float pp = sqrtf(p2 / 6.f);
+    const float b00 = f00 / pp, b01 = f01 / pp, b02 = f02 / pp, b11 = f11 / pp, b12 = f12 / pp, b22 = f22 / pp;
+    float r = (b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02)) / 2.f;
+    r = fminf(1.f, fmaxf(-1.f, r));
+    lam32 = 2.f * pp * cosf(acosf(r) / 3.f);
+  }
+  const double t2 = 0.5 * (a00 * a00 + a11 * a11 + a22 * a22 + 2.0 * (a01 * a01 + a02 * a02 + a12 * a12));
+  const double det = a00 * (a11 * a22 - a12 * a12) - a01 * (a01 * a22 - a12 * a02) + a02 * (a01 * a12 - a11 * a02);
+  double lam = (double)lam32;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double f = -lam * lam * lam + t2 * lam + det;
+    const double df = -3.0 * lam * lam + t2;
+    if (df != 0.0) lam -= f / df;
+  }
+  return lam;
+}
+
 template <typename T>
 __device__ void principal_dir(const T* q, T n[3]) {
   T a00 = q[0], a01 = q[1], a02 = q[2], a11 = q[3], a12 = q[4], a22 = -q[0] - q[3];
@@ -194,13 +262,18 @@ __device__ void principal_dir(const T* q, T n[3]) {
     n[0] = T(1); n[1] = T(0); n[2] = T(0);
     return;
   }
-  T p = sqrt(p2 / T(6));
-  T b00 = a00 / p, b01 = a01 / p, b02 = a02 / p, b11 = a11 / p, b12 = a12 / p, b22 = a22 / p;
-  T det = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
-  T r = det / T(2);
-  r = r < T(-1) ? T(-1) : (r > T(1) ? T(1) : r);
-  T phi = acos(r) / T(3);
-  T lam = T(2) * p * cos(phi);
+  T lam;
+  if constexpr (sizeof(T) == 8) {
+    lam = principal_lambda_f64(q);
+  } else {
+    T p = sqrt(p2 / T(6));
+    T b00 = a00 / p, b01 = a01 / p, b02 = a02 / p, b11 = a11 / p, b12 = a12 / p, b22 = a22 / p;
+    T det = b00 * (b11 * b22 - b12 * b12) - b01 * (b01 * b22 - b12 * b02) + b02 * (b01 * b12 - b11 * b02);
+    T r = det / T(2);
+    r = r < T(-1) ? T(-1) : (r > T(1) ? T(1) : r);
+    T phi = acos(r) / T(3);
+    lam = T(2) * p * cos(phi);
+  }
   T r0[3] = {a00 - lam, a01, a02}, r1[3] = {a01, a11 - lam, a12}, r2[3] = {a02, a12, a22 - lam};
   T c0[3] = {r0[1] * r1[2] - r0[2] * r1[1], r0[2] * r1[0] - r0[0] * r1[2], r0[0] * r1[1] - r0[1] * r1[0]};
   T c1[3] = {r0[1] * r2[2] - r0[2] * r2[1], r0[2] * r2[0] - r0[0] * r2[2], r0[0] * r2[1] - r0[1] * r2[0]};
@@ -371,6 +444,74 @@ __device__ __forceinline__ void gather_q(const DevBox& B, const T* __restrict__ 
   }
 }
 
+// FP32 storage, node next to a solid or wall: the derivatives from the
+// compensated values hi + lo of the node and of its face neighbours, each
+// neighbour difference formed as (hi_j - hi_i) + (lo_j - lo_i), and a solid
+// or wall neighbour's surface value as Q0 - Q_i scaled by w/(K + w) (1 for
+// strong anchoring), with Q0 and that difference in FP64.  With hi alone the rounding of Q (~3e-8) enters the
+// Laplacian of every node at the colloid surface, and the colloid's LC force,
+// a small sum of large face terms, would carry it at ~1e-4 relative.
+// qi receives the node's Q (hi + lo in FP32).
+__device__ __forceinline__ void near_derivatives_f32(const DevBox& B, int x, int y, int z, int i, float qi[5],
+                                                     float dq[3][5], float lap[5]) {
+  const int N = B.N, qpar = B.st->qpar;
+  const float* __restrict__ Q = static_cast<const float*>(B.Q[qpar]);
+  const __nv_bfloat16* __restrict__ Lo = B.Qlo[qpar];
+  float qh[5], ql[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    qh[k] = __ldg(Q + (size_t)k * N + i);
+    ql[k] = __bfloat162float(Lo[(size_t)k * N + i]);
+    qi[k] = qh[k] + ql[k];
+  }
+  int nb[6], zz[2];
+  face_neighbours(B, x, y, z, nb, zz);
+  const int nx = B.nx, ny = B.ny;
+  float dn[6][5];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const int j = nb[d];
+    int c = -1;
+    bool solid = true;
+    if (j >= 0) {
+      const uint8_t mj = B.mask[j] & IDMASK;
+      solid = mj != 0;
+      c = (int)mj - 1;
+    }
+    if (!solid) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        dn[d][k] = (__ldg(Q + (size_t)k * N + j) - qh[k]) + (__bfloat162float(Lo[(size_t)k * N + j]) - ql[k]);
+    } else {
+      int sx = x, sy = y, sz = z;
+      if (d == 0) sx = x + 1 == nx ? 0 : x + 1;
+      if (d == 1) sx = x == 0 ? nx - 1 : x - 1;
+      if (d == 2) sy = y + 1 == ny ? 0 : y + 1;
+      if (d == 3) sy = y == 0 ? ny - 1 : y - 1;
+      if (d == 4) sz = zz[0];
+      if (d == 5) sz = zz[1];
+      // the surface value in FP64: its normal (and for planar anchoring the
+      // director of Q) enter the face term at the same order as the rounding
+      // this path avoids
+      double qid[5], q0[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) qid[k] = (double)qh[k] + (double)ql[k];
+      surface_q0<double>(B, c, sx, sy, sz, qid, q0);
+      const bool strong = (c < 0) || B.col[c].strong;
+      const double s = strong ? 1.0 : B.col[c].w / (B.pd.K + B.col[c].w);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) dn[d][k] = (float)(s * ((q0[k] - (double)qh[k]) - (double)ql[k]));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    dq[0][k] = 0.5f * (dn[0][k] - dn[1][k]);
+    dq[1][k] = 0.5f * (dn[2][k] - dn[3][k]);
+    dq[2][k] = 0.5f * (dn[4][k] - dn[5][k]);
+    lap[k] = (dn[0][k] + dn[1][k]) + (dn[2][k] + dn[3][k]) + (dn[4][k] + dn[5][k]);
+  }
+}
+
 // Derivatives from the face-neighbour values: central first differences
 // dq[g][k] = d_g Q_k and the 7-point Laplacian (Sec. 2.2: one stencil at all
 // fluid nodes, surface values standing in for solid neighbours).
@@ -492,10 +633,21 @@ __device__ __forceinline__ void stress(const PhysT<T>& P, const T q[5], const T 
 //         A = Q H,  E_ab = K <d_a Q, d_b Q> + 2 K q0 sum_gn d_a Q_gn eps_mbg Q_mn  (Eq. 4)
 // The same expressions as molecular_field / free_energy_density / stress.
 template <typename T, bool NEED_P>
+__device__ __forceinline__ void lc_node_d(const PhysT<T>& P, const T qi[5], const T dq[3][5], const T lap[5], T h[5],
+                                          T p[9], T* fprime);
+
+template <typename T, bool NEED_P>
 __device__ __forceinline__ void lc_node(const PhysT<T>& P, const T qi[5], const T qn[6][5], T h[5], T p[9],
                                         T* fprime) {
   T dq[3][5], lap[5];
   derivatives(qi, qn, dq, lap);
+  lc_node_d<T, NEED_P>(P, qi, dq, lap, h, p, fprime);
+}
+
+// The same from the derivatives dq[g][k] = d_g Q_k and the Laplacian lap[k].
+template <typename T, bool NEED_P>
+__device__ __forceinline__ void lc_node_d(const PhysT<T>& P, const T qi[5], const T dq[3][5], const T lap[5], T h[5],
+                                          T p[9], T* fprime) {
   const T A0 = P.A0, g = P.gamma, K = P.K, q0 = P.q0;
   T Q[3][3], D[3][3][3], S2[3][3], C[3][3];
 #pragma unroll

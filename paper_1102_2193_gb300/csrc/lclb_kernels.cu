@@ -19,6 +19,16 @@ namespace lclb {
 
 constexpr int TX = 32;
 
+// Loads of data that the same launch may have written (the persistent step
+// kernel: stress, velocity, post-collision populations, colloid sums) go
+// through L2 only (CG); data produced by earlier launches may take the
+// read-only path.
+template <bool CG, typename T>
+__device__ __forceinline__ T ldx(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return __ldg(p);
+}
+
 // ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
@@ -413,7 +423,7 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * 
 // neighbour is not held by the adjacent lane (the tile's edge lanes, the
 // periodic wrap, the end of a ragged row) loads it.  All 32 lanes call this.
 // xn[0] = x + 1, xn[1] = x - 1 (the order of face_neighbours).
-template <typename T, int K>
+template <typename T, int K, bool CG = false>
 __device__ __forceinline__ void x_neighbours(const T* __restrict__ F, size_t N, const T self[K], int lane, int x,
                                              int nx, int row, bool valid, T xn[2][K]) {
 #pragma unroll
@@ -425,12 +435,12 @@ __device__ __forceinline__ void x_neighbours(const T* __restrict__ F, size_t N, 
   if (lane == TX - 1 || x + 1 >= nx) {
     const int j = (x + 1 == nx ? 0 : x + 1) + row;
 #pragma unroll
-    for (int k = 0; k < K; ++k) xn[0][k] = ldg(F + (size_t)k * N + j);
+    for (int k = 0; k < K; ++k) xn[0][k] = ldx<CG>(F + (size_t)k * N + j);
   }
   if (lane == 0) {
     const int j = (x == 0 ? nx - 1 : x - 1) + row;
 #pragma unroll
-    for (int k = 0; k < K; ++k) xn[1][k] = ldg(F + (size_t)k * N + j);
+    for (int k = 0; k < K; ++k) xn[1][k] = ldx<CG>(F + (size_t)k * N + j);
   }
 }
 
@@ -482,11 +492,49 @@ __device__ __forceinline__ void column_roll(T cz[2][K], const T pc[5][K]) {
 // A plain node (NEAR_NODE false) takes its own Q and that of its x- and
 // z-neighbours from pq (self, x + 1, x - 1, z + 1, z - 1: gathered by the warp
 // and rolled down the thread's column) and loads the y-neighbours.
+// FP32 node next to a solid or wall: derivatives from the compensated Q
+// (near_derivatives_f32), H and P stored, colloid faces summed.  Every node
+// of the shell around a colloid or along a wall takes this path: the
+// colloid's LC force is a small sum of large face terms, and the body force
+// at the boundary links, which sets the hydrodynamic force, is the face
+// divergence of the stress of these nodes.  Not inlined, so that the wider
+// arithmetic of this rare path does not raise the register count of the
+// plain path of the stress kernels.
+__device__ __noinline__ void near_stress_f32(const DevBox& B, float* __restrict__ Hb, float* __restrict__ Pb, int x,
+                                             int y, int z, int i, int mode, int& my_c, double my_acc[6]) {
+  const int N = B.N;
+  float qi[5], dq[3][5], lap[5], h[5], p[9], fp;
+  near_derivatives_f32(B, x, y, z, i, qi, dq, lap);
+  lc_node_d<float, true>(B.pf, qi, dq, lap, h, p, &fp);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) Hb[(size_t)c * N + i] = h[c];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) Pb[(size_t)c * N + i] = p[c];
+  if (mode & FORCE_ACC) {
+    int nb[6], zz[2];
+    face_neighbours(B, x, y, z, nb, zz);
+    for (int d = 0; d < 6; ++d) {
+      const int j = nb[d];
+      if (j < 0) continue;
+      const uint8_t fj = B.mask[j] & IDMASK;
+      if (fj == 0) continue;
+      const int ax = d >> 1;
+      const float sgn = (d & 1) ? -1.f : 1.f;
+      const float pcv[3] = {p[ax], p[3 + ax], p[6 + ax]};
+      colloid_face(B, fj - 1, ax, sgn, pcv, x, y, z, my_c, my_acc);
+    }
+  }
+}
+
 template <typename T, bool NEAR_NODE>
 __device__ __forceinline__ void stress_node(const DevBox& B, const PhysT<T>& PP, const T* __restrict__ Q,
                                             T* __restrict__ Hb, T* __restrict__ Pb, int x, int y, int z, int i,
                                             uint8_t m, int mode, int& my_c, double my_acc[6],
                                             const T (*pq)[5] = nullptr) {
+  if constexpr (NEAR_NODE && sizeof(T) == 4) {
+    near_stress_f32(B, Hb, Pb, x, y, z, i, mode, my_c, my_acc);
+    return;
+  }
   const int N = B.N;
   T qi[5], qn[6][5], h[5], p[9], fp;
   if (NEAR_NODE) {
@@ -535,62 +583,68 @@ __device__ __forceinline__ void stress_node(const DevBox& B, const PhysT<T>& PP,
 // time, so a row that crosses a colloid does not run the surface path with
 // most of its lanes idle.
 template <typename T, int TY>
-__global__ void __launch_bounds__(TX * TY) k_stress(const DevBox* __restrict__ boxes, const int4* __restrict__ tiles,
-                                                    int ntiles, int zc, int mode, double* __restrict__ part) {
+__device__ __forceinline__ void stress_tile(const DevBox& B, const int4 td, int zc, int mode, int (*sq)[2 * TX]) {
+  if (!B.p.lc_on) return;
+  const int lane = threadIdx.x, wy = threadIdx.y;
+  const PhysT<T>& PP = phys<T>(B);
+  const T* __restrict__ Q = static_cast<const T*>(B.Q[B.st->qpar]);
+  T* __restrict__ Hb = static_cast<T*>(B.H);
+  T* __restrict__ Pb = static_cast<T*>(B.P);
+  const int nx = B.nx, ny = B.ny;
+  const int x = td.y + lane, y = td.z + wy;
+  const int zend = min(td.w + zc, B.nz);
+  const bool valid = x < nx && y < ny;
+  int my_c = -1;
+  double my_acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int nq = 0;  // queued near nodes of this warp (warp-uniform)
+  T qz[2][5];  // Q of the thread's own column at z - 1 and z, rolled down the z march
+  column_start<T, 5>(B, Q, x, y, td.w, valid, qz);
+  for (int z = td.w; z < zend; ++z) {
+    const int i = x + nx * (y + ny * z);
+    const uint8_t m = valid ? B.mask[i] : (uint8_t)1;
+    const bool fluid = (m & IDMASK) == 0;
+    const bool near = fluid && (m & NEAR);
+    T pq[5][5];
+    column_next<T, 5>(B, Q, x, y, z, valid, qz, pq);
+    x_neighbours<T, 5>(Q, (size_t)B.N, pq[0], lane, x, nx, nx * (y + ny * z), valid, &pq[1]);
+    if (fluid && !near) stress_node<T, false>(B, PP, Q, Hb, Pb, x, y, z, i, m, mode, my_c, my_acc, pq);
+    const unsigned nb = __ballot_sync(0xffffffffu, near);
+    if (nb) {
+      if (near) sq[wy][nq + __popc(nb & ((1u << lane) - 1u))] = i;
+      nq += __popc(nb);
+      __syncwarp();
+      if (nq >= TX) {
+        const int j = sq[wy][lane];
+        const int jx = j % nx, jy = (j / nx) % ny, jz = j / (nx * ny);
+        stress_node<T, true>(B, PP, Q, Hb, Pb, jx, jy, jz, j, B.mask[j], mode, my_c, my_acc);
+        __syncwarp();
+        nq -= TX;
+        if (lane < nq) sq[wy][lane] = sq[wy][TX + lane];
+        __syncwarp();
+      }
+    }
+    column_roll<T, 5>(qz, pq);
+  }
+  if (lane < nq) {
+    const int j = sq[wy][lane];
+    const int jx = j % nx, jy = (j / nx) % ny, jz = j / (nx * ny);
+    stress_node<T, true>(B, PP, Q, Hb, Pb, jx, jy, jz, j, B.mask[j], mode, my_c, my_acc);
+  }
+  __syncwarp();
+  if (mode & FORCE_ACC) warp_flush_colloid(B.col, my_c, my_acc, 6);
+}
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 : 256) / (TX * TY)) k_stress(
+    const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
+    double* __restrict__ part) {
   __shared__ DevBox B;
   __shared__ int sq[TY][2 * TX];  // per-warp queue of near fluid nodes
-  const int lane = threadIdx.x, wy = threadIdx.y;
   int cur_box = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
     load_box(B, boxes, td.x, cur_box);
-    if (!B.p.lc_on) continue;
-    const PhysT<T>& PP = phys<T>(B);
-    const T* __restrict__ Q = static_cast<const T*>(B.Q[B.st->qpar]);
-    T* __restrict__ Hb = static_cast<T*>(B.H);
-    T* __restrict__ Pb = static_cast<T*>(B.P);
-    const int nx = B.nx, ny = B.ny;
-    const int x = td.y + lane, y = td.z + wy;
-    const int zend = min(td.w + zc, B.nz);
-    const bool valid = x < nx && y < ny;
-    int my_c = -1;
-    double my_acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    int nq = 0;  // queued near nodes of this warp (warp-uniform)
-    T qz[2][5];  // Q of the thread's own column at z - 1 and z, rolled down the z march
-    column_start<T, 5>(B, Q, x, y, td.w, valid, qz);
-    for (int z = td.w; z < zend; ++z) {
-      const int i = x + nx * (y + ny * z);
-      const uint8_t m = valid ? B.mask[i] : (uint8_t)1;
-      const bool fluid = (m & IDMASK) == 0;
-      const bool near = fluid && (m & NEAR);
-      T pq[5][5];
-      column_next<T, 5>(B, Q, x, y, z, valid, qz, pq);
-      x_neighbours<T, 5>(Q, (size_t)B.N, pq[0], lane, x, nx, nx * (y + ny * z), valid, &pq[1]);
-      if (fluid && !near) stress_node<T, false>(B, PP, Q, Hb, Pb, x, y, z, i, m, mode, my_c, my_acc, pq);
-      const unsigned nb = __ballot_sync(0xffffffffu, near);
-      if (nb) {
-        if (near) sq[wy][nq + __popc(nb & ((1u << lane) - 1u))] = i;
-        nq += __popc(nb);
-        __syncwarp();
-        if (nq >= TX) {
-          const int j = sq[wy][lane];
-          const int jx = j % nx, jy = (j / nx) % ny, jz = j / (nx * ny);
-          stress_node<T, true>(B, PP, Q, Hb, Pb, jx, jy, jz, j, B.mask[j], mode, my_c, my_acc);
-          __syncwarp();
-          nq -= TX;
-          if (lane < nq) sq[wy][lane] = sq[wy][TX + lane];
-          __syncwarp();
-        }
-      }
-      column_roll<T, 5>(qz, pq);
-    }
-    if (lane < nq) {
-      const int j = sq[wy][lane];
-      const int jx = j % nx, jy = (j / nx) % ny, jz = j / (nx * ny);
-      stress_node<T, true>(B, PP, Q, Hb, Pb, jx, jy, jz, j, B.mask[j], mode, my_c, my_acc);
-    }
-    __syncwarp();
-    if (mode & FORCE_ACC) warp_flush_colloid(B.col, my_c, my_acc, 6);
+    stress_tile<T, TY>(B, td, zc, mode, sq);
   }
 }
 
@@ -598,7 +652,7 @@ __global__ void __launch_bounds__(TX * TY) k_stress(const DevBox* __restrict__ b
 // k_flb, sum over the six faces of +-(face value), the face value the mean of
 // the two nodes' P or, across a solid or wall face, P(i).  With six fluid
 // neighbours the P(i) halves cancel.
-template <typename T>
+template <typename T, bool CG = false>
 __device__ __forceinline__ void stored_force(const DevBox& B, const T* __restrict__ Pb, int x, int y, int z, int i,
                                              uint8_t m, T F[3]) {
   const size_t N = (size_t)B.N;
@@ -608,8 +662,8 @@ __device__ __forceinline__ void stored_force(const DevBox& B, const T* __restric
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const T* Pa = Pb + (size_t)(3 * a) * N;
-      F[a] = T(0.5) * ((ldg(Pa + nb[0]) - ldg(Pa + nb[1])) + (ldg(Pa + N + nb[2]) - ldg(Pa + N + nb[3])) +
-                       (ldg(Pa + 2 * N + nb[4]) - ldg(Pa + 2 * N + nb[5])));
+      F[a] = T(0.5) * ((ldx<CG>(Pa + nb[0]) - ldx<CG>(Pa + nb[1])) + (ldx<CG>(Pa + N + nb[2]) - ldx<CG>(Pa + N + nb[3])) +
+                       (ldx<CG>(Pa + 2 * N + nb[4]) - ldx<CG>(Pa + 2 * N + nb[5])));
     }
     return;
   }
@@ -623,8 +677,8 @@ __device__ __forceinline__ void stored_force(const DevBox& B, const T* __restric
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const T* Pc = Pb + (size_t)(3 * a + ax) * N;
-      const T pc = ldg(Pc + i);
-      const T face = fluid ? T(0.5) * (pc + ldg(Pc + j)) : pc;
+      const T pc = ldx<CG>(Pc + i);
+      const T face = fluid ? T(0.5) * (pc + ldx<CG>(Pc + j)) : pc;
       F[a] += sgn * face;
     }
   }
@@ -633,7 +687,7 @@ __device__ __forceinline__ void stored_force(const DevBox& B, const T* __restric
 // One fluid node of k_lbp: pull (bounce-back only for near nodes), body force
 // from the stored P, collide, store.  For a plain node the mask handed down
 // has the near bit cleared, which removes the neighbour checks at compile time.
-template <typename T, bool NEAR_NODE>
+template <typename T, bool NEAR_NODE, bool CG = false>
 __device__ __forceinline__ void lbp_node(const DevBox& B, const PhysT<T>& PP, const T* __restrict__ fin,
                                          T* __restrict__ fout, const T* __restrict__ Pb, T* __restrict__ ub, int x,
                                          int y, int z, int i, uint8_t m, bool pre, bool lc) {
@@ -643,7 +697,7 @@ __device__ __forceinline__ void lbp_node(const DevBox& B, const PhysT<T>& PP, co
   T Fx = PP.g[0], Fy = PP.g[1], Fz = PP.g[2];
   if (lc) {
     T Fv[3];
-    stored_force(B, Pb, x, y, z, i, mm, Fv);
+    stored_force<T, CG>(B, Pb, x, y, z, i, mm, Fv);
     Fx += Fv[0];
     Fy += Fv[1];
     Fz += Fv[2];
@@ -654,58 +708,63 @@ __device__ __forceinline__ void lbp_node(const DevBox& B, const PhysT<T>& PP, co
 // k_lbp: like k_stress, a warp collides the plain fluid nodes of its row
 // together and queues the nodes next to a solid or wall (bounce-back links,
 // solid faces of the force) in shared memory, 32 at a time.
+template <typename T, int TY, bool CG>
+__device__ __forceinline__ void lbp_tile(const DevBox& B, const int4 td, int zc, int (*sq)[2 * TX]) {
+  if (!B.p.flow_on) return;
+  const int lane = threadIdx.x, wy = threadIdx.y;
+  const PhysT<T>& PP = phys<T>(B);
+  const int fpar = B.st->fpar;
+  const bool pre = B.st->pre_valid != 0;
+  const T* __restrict__ fin = static_cast<const T*>(B.f[fpar]);
+  T* __restrict__ fout = static_cast<T*>(B.f[fpar ^ 1]);
+  const T* __restrict__ Pb = static_cast<const T*>(B.P);
+  T* __restrict__ ub = static_cast<T*>(B.u);
+  const int nx = B.nx, ny = B.ny;
+  const int x = td.y + lane, y = td.z + wy;
+  const int zend = min(td.w + zc, B.nz);
+  const bool valid = x < nx && y < ny;
+  const bool lc = B.p.lc_on != 0;
+  int nq = 0;
+  for (int z = td.w; z < zend; ++z) {
+    const int i = x + nx * (y + ny * z);
+    const uint8_t m = valid ? B.mask[i] : (uint8_t)0;
+    const bool fluid = valid && (m & IDMASK) == 0;
+    const bool near = fluid && (m & NEAR);
+    if (valid && !fluid) solid_velocity(B, ub, x, y, z, i, m);
+    if (fluid && !near) lbp_node<T, false, CG>(B, PP, fin, fout, Pb, ub, x, y, z, i, m, pre, lc);
+    const unsigned nb = __ballot_sync(0xffffffffu, near);
+    if (nb) {
+      if (near) sq[wy][nq + __popc(nb & ((1u << lane) - 1u))] = i;
+      nq += __popc(nb);
+      __syncwarp();
+      if (nq >= TX) {
+        const int j = sq[wy][lane];
+        lbp_node<T, true, CG>(B, PP, fin, fout, Pb, ub, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j], pre, lc);
+        __syncwarp();
+        nq -= TX;
+        if (lane < nq) sq[wy][lane] = sq[wy][TX + lane];
+        __syncwarp();
+      }
+    }
+  }
+  if (lane < nq) {
+    const int j = sq[wy][lane];
+    lbp_node<T, true, CG>(B, PP, fin, fout, Pb, ub, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j], pre, lc);
+  }
+  __syncwarp();
+}
+
 template <typename T, int TY>
 __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 : 384) / (TX * TY)) k_lbp(
     const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
     double* __restrict__ part) {
   __shared__ DevBox B;
   __shared__ int sq[TY][2 * TX];
-  const int lane = threadIdx.x, wy = threadIdx.y;
   int cur_box = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
     load_box(B, boxes, td.x, cur_box);
-    if (!B.p.flow_on) continue;
-    const PhysT<T>& PP = phys<T>(B);
-    const int fpar = B.st->fpar;
-    const bool pre = B.st->pre_valid != 0;
-    const T* __restrict__ fin = static_cast<const T*>(B.f[fpar]);
-    T* __restrict__ fout = static_cast<T*>(B.f[fpar ^ 1]);
-    const T* __restrict__ Pb = static_cast<const T*>(B.P);
-    T* __restrict__ ub = static_cast<T*>(B.u);
-    const int nx = B.nx, ny = B.ny;
-    const int x = td.y + lane, y = td.z + wy;
-    const int zend = min(td.w + zc, B.nz);
-    const bool valid = x < nx && y < ny;
-    const bool lc = B.p.lc_on != 0;
-    int nq = 0;
-    for (int z = td.w; z < zend; ++z) {
-      const int i = x + nx * (y + ny * z);
-      const uint8_t m = valid ? B.mask[i] : (uint8_t)0;
-      const bool fluid = valid && (m & IDMASK) == 0;
-      const bool near = fluid && (m & NEAR);
-      if (valid && !fluid) solid_velocity(B, ub, x, y, z, i, m);
-      if (fluid && !near) lbp_node<T, false>(B, PP, fin, fout, Pb, ub, x, y, z, i, m, pre, lc);
-      const unsigned nb = __ballot_sync(0xffffffffu, near);
-      if (nb) {
-        if (near) sq[wy][nq + __popc(nb & ((1u << lane) - 1u))] = i;
-        nq += __popc(nb);
-        __syncwarp();
-        if (nq >= TX) {
-          const int j = sq[wy][lane];
-          lbp_node<T, true>(B, PP, fin, fout, Pb, ub, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j], pre, lc);
-          __syncwarp();
-          nq -= TX;
-          if (lane < nq) sq[wy][lane] = sq[wy][TX + lane];
-          __syncwarp();
-        }
-      }
-    }
-    if (lane < nq) {
-      const int j = sq[wy][lane];
-      lbp_node<T, true>(B, PP, fin, fout, Pb, ub, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j], pre, lc);
-    }
-    __syncwarp();
+    lbp_tile<T, TY, false>(B, td, zc, sq);
   }
 }
 
@@ -814,12 +873,21 @@ __global__ void __launch_bounds__(32 * (BY + 3), (sizeof(T) == 4 && BY <= 4) ? 2
 // Holding the z-neighbours in registers down the z march, as the stress
 // kernel does, pushed this kernel past its 96-register cap (spills, 76 us
 // against 71 us).
-template <typename T, bool NEAR_NODE>
+template <typename T, bool NEAR_NODE, bool CG = false>
 __device__ __forceinline__ void lc_update_node(const DevBox& B, const PhysT<T>& PP, const T* __restrict__ Q,
-                                               T* __restrict__ Qo, const T* __restrict__ U, int x, int y, int z,
-                                               int i, uint8_t m, T& rsum, T& rmax, const T (*pq)[5] = nullptr,
-                                               const T (*pu)[3] = nullptr) {
+                                               T* __restrict__ Qo, const __nv_bfloat16* __restrict__ Lin,
+                                               __nv_bfloat16* __restrict__ Lout, const T* __restrict__ U, int x,
+                                               int y, int z, int i, uint8_t m, T& rsum, T& rmax,
+                                               const T (*pq)[5] = nullptr, const T (*pu)[3] = nullptr,
+                                               const float* plo = nullptr) {
   const int N = B.N;
+  // BF16 remainder of the node's own Q (FP32 storage), loaded with the other
+  // inputs so that its latency overlaps theirs
+  float lo[5];
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) lo[c] = NEAR_NODE ? __bfloat162float(Lin[(size_t)c * N + i]) : plo[c];
+  }
   const T Gam = PP.Gamma, xi = PP.xi;
   // H of this node was stored by the stress kernel of this step; Q of the
   // fluid face neighbours is needed only for the advective fluxes (zero
@@ -829,14 +897,14 @@ __device__ __forceinline__ void lc_update_node(const DevBox& B, const PhysT<T>& 
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     qi[c] = NEAR_NODE ? ldg(Q + (size_t)c * N + i) : pq[0][c];
-    h[c] = Hb[(size_t)c * N + i];
+    h[c] = ldx<CG>(Hb + (size_t)c * N + i);
   }
   int nb[6], zz[2];
   face_neighbours(B, x, y, z, nb, zz);
   T ui[3], un[6][3];
   bool fl[6];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) ui[a] = NEAR_NODE ? ldg(U + (size_t)a * N + i) : pu[0][a];
+  for (int a = 0; a < 3; ++a) ui[a] = NEAR_NODE ? ldx<CG>(U + (size_t)a * N + i) : pu[0][a];
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     const int j = nb[d];
@@ -849,7 +917,7 @@ __device__ __forceinline__ void lc_update_node(const DevBox& B, const PhysT<T>& 
       continue;
     }
 #pragma unroll
-    for (int a = 0; a < 3; ++a) un[d][a] = (!NEAR_NODE || j >= 0) ? ldg(U + (size_t)a * N + j) : T(0);
+    for (int a = 0; a < 3; ++a) un[d][a] = (!NEAR_NODE || j >= 0) ? ldx<CG>(U + (size_t)a * N + j) : T(0);
 #pragma unroll
     for (int c = 0; c < 5; ++c) qn[d][c] = fl[d] ? ldg(Q + (size_t)c * N + j) : T(0);
   }
@@ -905,13 +973,57 @@ __device__ __forceinline__ void lc_update_node(const DevBox& B, const PhysT<T>& 
     }
   const T tr = dQ[0][0] + dQ[1][1] + dQ[2][2];
   const int ia[5] = {0, 0, 0, 1, 1}, ib[5] = {0, 1, 2, 1, 2};
+  if constexpr (sizeof(T) == 4) {
+    // H was evaluated at hi; the stored Q is hi + lo.  Add the local part of
+    // H(hi + lo) - H(hi) to first order: the bulk terms' derivative at hi
+    // applied to lo, and lo's own term -6 K lo of the Laplacian (the
+    // neighbours' lo enter K lap and the gradient terms at the ~1e-9 level).
+    // Without it the relaxation stalls where A0 lo ~ the residual.
+    const T A0 = PP.A0, g = PP.gamma, K = PP.K, q0 = PP.q0;
+    T Qm[3][3], Lm[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        Qm[a][b] = qab(qi, a, b);
+        Lm[a][b] = qab(lo, a, b);
+      }
+    T trq2 = T(0), trql = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        trq2 += Qm[a][b] * Qm[a][b];
+        trql += Qm[a][b] * Lm[a][b];
+      }
+    const T cb = -A0 * (T(1) - g / T(3)) - A0 * g * trq2 - T(4) * K * q0 * q0 - T(6) * K;
+    const T A0g = A0 * g;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int a = ia[k], b = ib[k];
+      T ql = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ql += Qm[a][c] * Lm[c][b] + Lm[a][c] * Qm[c][b];
+      if (a == b) ql -= T(2) / T(3) * trql;
+      h[k] += cb * lo[k] + A0g * ql - T(2) * A0g * trql * qi[k];
+    }
+  }
   T d5[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     T v = Gam * h[k] + dQ[ia[k]][ib[k]] - adv[k];
     if (ia[k] == ib[k]) v -= tr / T(3);
     d5[k] = v;
-    Qo[(size_t)k * N + i] = qi[k] + v;
+    if constexpr (sizeof(T) == 4) {
+      // compensated FP32 storage: hi + lo + increment carried exactly into hi, to BF16 in lo
+      float hi;
+      __nv_bfloat16 lo_out;
+      add_compensated(qi[k], lo[k], v, hi, lo_out);
+      Qo[(size_t)k * N + i] = hi;
+      Lout[(size_t)k * N + i] = lo_out;
+    } else {
+      Qo[(size_t)k * N + i] = qi[k] + v;
+    }
   }
   const T dzz = -d5[0] - d5[3];
   rsum += d5[0] * d5[0] + d5[3] * d5[3] + dzz * dzz + T(2) * (d5[1] * d5[1] + d5[2] * d5[2] + d5[4] * d5[4]);
@@ -922,7 +1034,79 @@ __device__ __forceinline__ void lc_update_node(const DevBox& B, const PhysT<T>& 
 }
 
 // k_lc: Beris-Edwards update; plain nodes of a warp's row together, nodes
-// next to a solid or wall queued and updated 32 at a time.
+// next to a solid or wall queued and updated 32 at a time.  part (if non-null)
+// receives the tile's residual partials (sum of squares, max).
+template <typename T, int TY, bool CG>
+__device__ __forceinline__ void lc_tile(const DevBox& B, const int4 td, int zc, double* part, double* sred,
+                                        int (*sq)[2 * TX]) {
+  if (!B.p.lc_on) return;
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const int lane = threadIdx.x, wy = threadIdx.y;
+  const int qpar = B.st->qpar;
+  const T* __restrict__ Q = static_cast<const T*>(B.Q[qpar]);
+  T* __restrict__ Qo = static_cast<T*>(B.Q[qpar ^ 1]);
+  const __nv_bfloat16* __restrict__ Lin = B.Qlo[qpar];
+  __nv_bfloat16* __restrict__ Lout = B.Qlo[qpar ^ 1];
+  const T* __restrict__ U = static_cast<const T*>(B.u);
+  const int nx = B.nx, ny = B.ny;
+  const int x = td.y + lane, y = td.z + wy;
+  const int zend = min(td.w + zc, B.nz);
+  const bool valid = x < nx && y < ny;
+  const PhysT<T>& PP = phys<T>(B);
+  T rsum = T(0), rmax = T(0);  // per-thread residual (sum of squares, max), in T
+  int nq = 0;
+  for (int z = td.w; z < zend; ++z) {
+    const int i = x + nx * (y + ny * z);
+    const uint8_t m = valid ? B.mask[i] : (uint8_t)1;
+    const bool fluid = (m & IDMASK) == 0;
+    const bool near = fluid && (m & NEAR);
+    T pq[3][5], pu[3][3];
+    float plo[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) pq[0][k] = valid ? ldg(Q + (size_t)k * B.N + i) : T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) pu[0][a] = valid ? ldx<CG>(U + (size_t)a * B.N + i) : T(0);
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) plo[k] = (valid && fluid && !near) ? __bfloat162float(Lin[(size_t)k * B.N + i]) : 0.f;
+    }
+    const int row = nx * (y + ny * z);
+    x_neighbours<T, 5>(Q, (size_t)B.N, pq[0], lane, x, nx, row, valid, &pq[1]);
+    x_neighbours<T, 3, CG>(U, (size_t)B.N, pu[0], lane, x, nx, row, valid, &pu[1]);
+    if (fluid && !near)
+      lc_update_node<T, false, CG>(B, PP, Q, Qo, Lin, Lout, U, x, y, z, i, m, rsum, rmax, pq, pu, plo);
+    const unsigned nb = __ballot_sync(0xffffffffu, near);
+    if (nb) {
+      if (near) sq[wy][nq + __popc(nb & ((1u << lane) - 1u))] = i;
+      nq += __popc(nb);
+      __syncwarp();
+      if (nq >= TX) {
+        const int j = sq[wy][lane];
+        lc_update_node<T, true, CG>(B, PP, Q, Qo, Lin, Lout, U, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j],
+                                    rsum, rmax);
+        __syncwarp();
+        nq -= TX;
+        if (lane < nq) sq[wy][lane] = sq[wy][TX + lane];
+        __syncwarp();
+      }
+    }
+  }
+  if (lane < nq) {
+    const int j = sq[wy][lane];
+    lc_update_node<T, true, CG>(B, PP, Q, Qo, Lin, Lout, U, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j], rsum,
+                                rmax);
+  }
+  __syncwarp();
+  if (part) {
+    double rs[2] = {(double)rsum, (double)rmax};
+    block_sum<2>(rs, sred, true);
+    if (tid == 0) {
+      part[0] = rs[0];
+      part[1] = rs[1];
+    }
+  }
+}
+
 template <typename T, int TY>
 __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 640 : 256) / (TX * TY)) k_lc(
     const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
@@ -930,66 +1114,11 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 640 : 256) / (TX * 
   __shared__ DevBox B;
   __shared__ double sred[32 * 2];
   __shared__ int sq[TY][2 * TX];
-  const int tid = threadIdx.x + TX * threadIdx.y;
-  const int lane = threadIdx.x, wy = threadIdx.y;
   int cur_box = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
     load_box(B, boxes, td.x, cur_box);
-    if (!B.p.lc_on) continue;
-    const int qpar = B.st->qpar;
-    const T* __restrict__ Q = static_cast<const T*>(B.Q[qpar]);
-    T* __restrict__ Qo = static_cast<T*>(B.Q[qpar ^ 1]);
-    const T* __restrict__ U = static_cast<const T*>(B.u);
-    const int nx = B.nx, ny = B.ny;
-    const int x = td.y + lane, y = td.z + wy;
-    const int zend = min(td.w + zc, B.nz);
-    const bool valid = x < nx && y < ny;
-    const PhysT<T>& PP = phys<T>(B);
-    T rsum = T(0), rmax = T(0);  // per-thread residual (sum of squares, max), in T
-    int nq = 0;
-    for (int z = td.w; z < zend; ++z) {
-      const int i = x + nx * (y + ny * z);
-      const uint8_t m = valid ? B.mask[i] : (uint8_t)1;
-      const bool fluid = (m & IDMASK) == 0;
-      const bool near = fluid && (m & NEAR);
-      T pq[3][5], pu[3][3];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) pq[0][k] = valid ? ldg(Q + (size_t)k * B.N + i) : T(0);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) pu[0][a] = valid ? ldg(U + (size_t)a * B.N + i) : T(0);
-      const int row = nx * (y + ny * z);
-      x_neighbours<T, 5>(Q, (size_t)B.N, pq[0], lane, x, nx, row, valid, &pq[1]);
-      x_neighbours<T, 3>(U, (size_t)B.N, pu[0], lane, x, nx, row, valid, &pu[1]);
-      if (fluid && !near) lc_update_node<T, false>(B, PP, Q, Qo, U, x, y, z, i, m, rsum, rmax, pq, pu);
-      const unsigned nb = __ballot_sync(0xffffffffu, near);
-      if (nb) {
-        if (near) sq[wy][nq + __popc(nb & ((1u << lane) - 1u))] = i;
-        nq += __popc(nb);
-        __syncwarp();
-        if (nq >= TX) {
-          const int j = sq[wy][lane];
-          lc_update_node<T, true>(B, PP, Q, Qo, U, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j], rsum, rmax);
-          __syncwarp();
-          nq -= TX;
-          if (lane < nq) sq[wy][lane] = sq[wy][TX + lane];
-          __syncwarp();
-        }
-      }
-    }
-    if (lane < nq) {
-      const int j = sq[wy][lane];
-      lc_update_node<T, true>(B, PP, Q, Qo, U, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j], rsum, rmax);
-    }
-    __syncwarp();
-    if (mode & LC_RESID) {
-      double rs[2] = {(double)rsum, (double)rmax};
-      block_sum<2>(rs, sred, true);
-      if (tid == 0) {
-        part[2 * t] = rs[0];
-        part[2 * t + 1] = rs[1];
-      }
-    }
+    lc_tile<T, TY, false>(B, td, zc, (mode & LC_RESID) ? part + 2 * t : nullptr, sred, sq);
   }
 }
 
@@ -1000,35 +1129,33 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 640 : 256) / (TX * 
 // 6 w_b rho0 c_b.u_b), u_b the rigid velocity at r + c_b/2; torque
 // (r + c_b/2 - X) x dp.  The constant w_b rho0 part of 2 f*_b sums to zero
 // over a closed surface and is left out.
-template <typename T>
-__global__ void __launch_bounds__(256) k_links(const DevBox* __restrict__ boxes, const int2* __restrict__ chunks,
-                                               int nchunks) {
-  __shared__ DevBox B;
-  __shared__ double sblk[18];
-  __shared__ int sc0;
-  const int tid = threadIdx.x;
-  for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const int2 cd = chunks[ch];
-    load_box(B, boxes, cd.x);
-    if (!B.p.flow_on) continue;
-    const int nl = *B.nlinks;
-    const int l = cd.y + tid;
+// One chunk of links (box record B, first link l0, count n) by all threads of
+// the block; sblk holds 18 doubles, sc0 one int of shared memory.
+template <typename T, bool CG>
+__device__ __forceinline__ void links_chunk(const DevBox& B, int l0, int n, double* sblk, int* sc0) {
+  if (!B.p.flow_on) return;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  const int nl = *B.nlinks;
+  for (int base = l0; base < l0 + n; base += nthr) {
+    const int l = base + tid;
     int my_c = -1;
     bool mob = false;
     // dp (3), torque (3), then for mobile colloids the drag tensors zv, zw (6 + 6)
     double v[18];
 #pragma unroll
     for (int k = 0; k < 18; ++k) v[k] = 0.0;
-    // the chunk's first colloid is summed in shared memory (links are sorted by colloid)
-    if (tid < 18) sblk[tid] = 0.0;
-    if (tid == 0) sc0 = (cd.y < nl && cd.y < B.nlinks_cap) ? (int)B.link_col[cd.y] : -1;
+    // the sub-chunk's first colloid is summed in shared memory (links are sorted by colloid)
     __syncthreads();
-    if (l < nl && l < B.nlinks_cap) {
+    if (tid < 18) sblk[tid] = 0.0;
+    if (tid == 0) *sc0 = (base < nl && base < B.nlinks_cap) ? (int)B.link_col[base] : -1;
+    __syncthreads();
+    if (l < l0 + n && l < nl && l < B.nlinks_cap) {
       const int i = B.link_node[l];
       const int q = B.link_dir[l];
       const int c = B.link_col[l];
       const T* fout = static_cast<const T*>(B.f[B.st->fpar ^ 1]);
-      const double dfq = (double)fout[(size_t)q * B.N + i];
+      const double dfq = (double)ldx<CG>(fout + (size_t)q * B.N + i);
       const int x = i % B.nx, y = (i / B.nx) % B.ny, z = i / (B.nx * B.ny);
       int qx = 0, qy = 0, qz = 0;
       switch (q) {
@@ -1068,7 +1195,7 @@ __global__ void __launch_bounds__(256) k_links(const DevBox* __restrict__ boxes,
         }
       }
     }
-    const int c0 = sc0;
+    const int c0 = *sc0;
     const bool main = (my_c == c0) && c0 >= 0;
     const bool warp_main = __all_sync(0xffffffffu, main || my_c < 0);
     const bool warp_mob = __any_sync(0xffffffffu, mob);
@@ -1085,6 +1212,19 @@ __global__ void __launch_bounds__(256) k_links(const DevBox* __restrict__ boxes,
     }
     __syncthreads();
     if (tid < 18 && c0 >= 0 && sblk[tid] != 0.0) atomicAdd(&B.col[c0].acc[tid < 6 ? tid : tid + 6], sblk[tid]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_links(const DevBox* __restrict__ boxes, const int2* __restrict__ chunks,
+                                               int nchunks) {
+  __shared__ DevBox B;
+  __shared__ double sblk[18];
+  __shared__ int sc0;
+  for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int2 cd = chunks[ch];
+    load_box(B, boxes, cd.x);
+    links_chunk<T, false>(B, cd.y, LINK_CHUNK, sblk, &sc0);
   }
 }
 
@@ -1106,17 +1246,24 @@ __device__ void solve_sym3(const double* a, double s, const double* b, double* x
 // velocity-dependent part of the link force is taken at the new velocity:
 // V' = V + (M + zv)^{-1} (F_hyd + F_lc + F_ext), W' = W + (I + zw)^{-1} (T_hyd + T_lc).
 // ---------------------------------------------------------------------------
-__global__ void k_colloid(DevBox* __restrict__ boxes, int nboxes) {
-  const int b = blockIdx.x;
-  if (b >= nboxes) return;
-  DevBox& B = boxes[b];
-  for (int c = threadIdx.x; c < B.ncol; c += blockDim.x) {
+template <bool CG>
+__device__ __forceinline__ void colloid_box(DevBox& B, bool commit = true) {
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  if (!commit) {
+    for (int c = tid; c < B.ncol; c += nthr)
+      for (int k = 0; k < 24; ++k) B.col[c].acc[k] = 0.0;
+    return;
+  }
+  for (int c = tid; c < B.ncol; c += nthr) {
     DevColloid& C = B.col[c];
+    double acc[24];
+    for (int k = 0; k < 24; ++k) acc[k] = CG ? __ldcg(&C.acc[k]) : C.acc[k];
     for (int a = 0; a < 3; ++a) {
-      C.Fh[a] = C.acc[a];
-      C.Th[a] = C.acc[3 + a];
-      C.Flc[a] = C.acc[6 + a];
-      C.Tlc[a] = C.acc[9 + a];
+      C.Fh[a] = acc[a];
+      C.Th[a] = acc[3 + a];
+      C.Flc[a] = acc[6 + a];
+      C.Tlc[a] = acc[9 + a];
     }
     for (int a = 0; a < 3; ++a) {
       C.imp[a] += C.Fh[a] + C.Flc[a];
@@ -1130,8 +1277,8 @@ __global__ void k_colloid(DevBox* __restrict__ boxes, int nboxes) {
                             C.Fh[2] + C.Flc[2] + C.Fext[2]};
       const double tv[3] = {C.Th[0] + C.Tlc[0], C.Th[1] + C.Tlc[1], C.Th[2] + C.Tlc[2]};
       double dv[3], dw[3];
-      solve_sym3(C.acc + 12, C.M, fv, dv);
-      solve_sym3(C.acc + 18, C.I, tv, dw);
+      solve_sym3(acc + 12, C.M, fv, dv);
+      solve_sym3(acc + 18, C.I, tv, dw);
       for (int a = 0; a < 3; ++a) {
         C.V[a] += dv[a];
         C.W[a] += dw[a];
@@ -1147,7 +1294,7 @@ __global__ void k_colloid(DevBox* __restrict__ boxes, int nboxes) {
     }
     for (int k = 0; k < 24; ++k) C.acc[k] = 0.0;
   }
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     DevState* st = B.st;
     if (B.p.flow_on) {
       st->fpar ^= 1;
@@ -1156,6 +1303,90 @@ __global__ void k_colloid(DevBox* __restrict__ boxes, int nboxes) {
     if (B.p.lc_on) st->qpar ^= 1;
     st->step += 1;
     st->nchg = 0;
+  }
+}
+
+__global__ void k_colloid(DevBox* __restrict__ boxes, int nboxes) {
+  const int b = blockIdx.x;
+  if (b >= nboxes) return;
+  colloid_box<false>(boxes[b]);
+}
+
+// ---------------------------------------------------------------------------
+// k_step: one coupled step of every box as one persistent launch
+// ---------------------------------------------------------------------------
+// The blocks take work items in list order from an atomic counter.  The list
+// is ordered so that every item comes after the items it waits for (stress of
+// z chunks c - 1, c, c + 1 before the LB of chunk c; LB of c - 1, c, c + 1
+// before the Q update of c; all LB tiles before the link exchange; all tiles
+// and links before the colloid update), so the earliest unfinished item
+// never waits on an item no block has taken, and the launch cannot deadlock
+// whether or not all blocks are resident.  The phases of different chunks run
+// side by side, so the HBM-bound LB overlaps the arithmetic-bound stress and
+// Q update, and the stress, velocity and molecular field of a chunk are read
+// back while they are still in L2.  Waits are bounded: after spin_limit
+// polls the item is skipped (its outputs are then stale), *err is set and the
+// host reports a timeout.
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 : 256) / (TX * TY)) k_step(
+    DevBox* __restrict__ boxes, const StepItem* __restrict__ items, int nitems, int zc, unsigned* __restrict__ sync,
+    double* __restrict__ part, int spin_limit, int commit, int* __restrict__ err) {
+  __shared__ DevBox B;
+  __shared__ double sred[32 * 2];
+  __shared__ double sblk[18];
+  __shared__ int sq[TY][2 * TX];
+  __shared__ int s_item, s_ok, s_sc0;
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  int cur_box = -1;
+  for (;;) {
+    if (tid == 0) s_item = (int)atomicAdd(&sync[0], 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) break;
+    const StepItem I = items[it];
+    if (tid == 0) {
+      int ok = 1;
+      for (int k = 0; k < 4 && ok; ++k) {
+        if (I.wc[k] < 0) continue;
+        const unsigned target = (unsigned)I.wt[k];
+        for (int spin = 0; ld_acquire_u32(&sync[I.wc[k]]) < target; ++spin) {
+          // give up after spin_limit polls, or at once when another wait of
+          // this launch already gave up
+          if (spin >= spin_limit || ((spin & 255) == 255 && ld_acquire_u32(reinterpret_cast<unsigned*>(err)) != 0)) {
+            ok = 0;
+            break;
+          }
+          __nanosleep(100);
+        }
+      }
+      if (!ok) atomicOr(err, 1);
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (s_ok) {
+      load_box(B, boxes, I.box, cur_box);
+      const int4 td = make_int4(I.box, I.x0, I.y0, I.z0);
+      switch (I.kind) {
+        case ITEM_STRESS: stress_tile<T, TY>(B, td, zc, FORCE_ACC, sq); break;
+        case ITEM_LB: lbp_tile<T, TY, true>(B, td, zc, sq); break;
+        case ITEM_LC: lc_tile<T, TY, true>(B, td, zc, part + 2 * (size_t)I.part, sred, sq); break;
+        case ITEM_LINKS: links_chunk<T, true>(B, I.x0, LINK_CHUNK, sblk, &s_sc0); break;
+        default: colloid_box<true>(B, commit != 0); break;
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      if (I.dc[0] >= 0) atomicAdd(&sync[I.dc[0]], 1u);
+      if (I.dc[1] >= 0) atomicAdd(&sync[I.dc[1]], 1u);
+    }
   }
 }
 
@@ -1295,6 +1526,41 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t s) {
   return z ^ (z >> 31);
 }
 
+// Stores FP64 value v as component k of node i in both Q buffers (FP32:
+// compensated, hi and its BF16 remainder).
+template <typename T>
+__device__ __forceinline__ void store_q(const DevBox& B, int i, int k, double v) {
+  const size_t o = (size_t)k * B.N + i;
+  if constexpr (sizeof(T) == 4) {
+    float hi;
+    __nv_bfloat16 lo;
+    split_q(v, hi, lo);
+    static_cast<float*>(B.Q[0])[o] = hi;
+    static_cast<float*>(B.Q[1])[o] = hi;
+    B.Qlo[0][o] = lo;
+    B.Qlo[1][o] = lo;
+  } else {
+    static_cast<double*>(B.Q[0])[o] = v;
+    static_cast<double*>(B.Q[1])[o] = v;
+  }
+}
+
+// Stores FP64 value v as component k of node i of the current Q buffer only.
+template <typename T>
+__device__ __forceinline__ void store_q_cur(const DevBox& B, int i, int k, double v) {
+  const int qpar = B.st->qpar;
+  const size_t o = (size_t)k * B.N + i;
+  if constexpr (sizeof(T) == 4) {
+    float hi;
+    __nv_bfloat16 lo;
+    split_q(v, hi, lo);
+    static_cast<float*>(B.Q[qpar])[o] = hi;
+    B.Qlo[qpar][o] = lo;
+  } else {
+    static_cast<double*>(B.Q[qpar])[o] = v;
+  }
+}
+
 // kind 0: uniaxial along (n0,n1,n2); kind 1: helix along axis (int)n0.
 template <typename T>
 __global__ void k_init_q(DevBox* __restrict__ boxes, int b, int kind, double n0, double n1, double n2, double amp,
@@ -1321,14 +1587,11 @@ __global__ void k_init_q(DevBox* __restrict__ boxes, int b, int kind, double n0,
   const double v[5] = {__dmul_rn(S0, __dsub_rn(__dmul_rn(d[0], d[0]), third)), __dmul_rn(S0, __dmul_rn(d[0], d[1])),
                        __dmul_rn(S0, __dmul_rn(d[0], d[2])), __dmul_rn(S0, __dsub_rn(__dmul_rn(d[1], d[1]), third)),
                        __dmul_rn(S0, __dmul_rn(d[1], d[2]))};
-  T* Qa = static_cast<T*>(B.Q[0]);
-  T* Qb = static_cast<T*>(B.Q[1]);
   for (int k = 0; k < 5; ++k) {
     const uint64_t r = splitmix64((uint64_t)seed ^ (uint64_t)(5LL * i + k));
     const double u = (double)(r >> 11) * (1.0 / 9007199254740992.0);
     const double val = __dadd_rn(v[k], __dmul_rn(amp, __dsub_rn(2.0 * u, 1.0)));
-    Qa[(size_t)k * B.N + i] = T(val);
-    Qb[(size_t)k * B.N + i] = T(val);
+    store_q<T>(B, i, k, val);
   }
 }
 
@@ -1340,13 +1603,7 @@ __global__ void k_set_field(DevBox* __restrict__ boxes, int b, int which, const 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B.N) return;
   if (which == 0) {
-    T* Qa = static_cast<T*>(B.Q[0]);
-    T* Qb = static_cast<T*>(B.Q[1]);
-    for (int k = 0; k < 5; ++k) {
-      const T v = T(src[(size_t)k * B.N + i]);
-      Qa[(size_t)k * B.N + i] = v;
-      Qb[(size_t)k * B.N + i] = v;
-    }
+    for (int k = 0; k < 5; ++k) store_q<T>(B, i, k, src[(size_t)k * B.N + i]);
   } else {
     T* f = static_cast<T*>(B.f[B.st->fpar]);
     for (int q = 0; q < NQ; ++q) f[(size_t)q * B.N + i] = T(src[(size_t)q * B.N + i] - wq(q) * B.p.rho0);
@@ -1363,8 +1620,7 @@ __global__ void k_export(const DevBox* __restrict__ boxes, int b, int which, dou
   const uint8_t m = B.mask[i];
   const int x = i % B.nx, y = (i / B.nx) % B.ny, z = i / (B.nx * B.ny);
   if (which == EXP_Q) {
-    const T* Q = static_cast<const T*>(B.Q[B.st->qpar]);
-    for (int k = 0; k < 5; ++k) out[(size_t)k * N + i] = (double)Q[(size_t)k * N + i];
+    for (int k = 0; k < 5; ++k) out[(size_t)k * N + i] = load_q<T>(B, i, k);
     return;
   }
   if (which == EXP_SOLID) {
@@ -1436,9 +1692,8 @@ __global__ void __launch_bounds__(256) k_diag_state(const DevBox* __restrict__ b
         v[3] += cz(q) * (double)df[q];
       }
       v[4] = 1.0;
-      const T* Q = static_cast<const T*>(B.Q[B.st->qpar]);
       double q[5];
-      for (int k = 0; k < 5; ++k) q[k] = (double)Q[(size_t)k * B.N + i];
+      for (int k = 0; k < 5; ++k) q[k] = load_q<T>(B, i, k);
       // largest eigenvalue of the traceless symmetric Q (closed form, as in principal_dir)
       double a00 = q[0], a01 = q[1], a02 = q[2], a11 = q[3], a12 = q[4], a22 = -q[0] - q[3];
       double p1 = a01 * a01 + a02 * a02 + a12 * a12;
@@ -1584,7 +1839,6 @@ __global__ void __launch_bounds__(256) k_rd_apply(DevBox* __restrict__ boxes, in
     if (nchg == 0) continue;
     const int fpar = B.st->fpar;
     T* fpre = static_cast<T*>(B.f[fpar ^ 1]);
-    T* Q = static_cast<T*>(B.Q[B.st->qpar]);
     const int N = B.N;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nchg; k += gridDim.x * blockDim.x) {
       const int i = B.chg[2 * k], code = B.chg[2 * k + 1];
@@ -1630,7 +1884,7 @@ __global__ void __launch_bounds__(256) k_rd_apply(DevBox* __restrict__ boxes, in
         if (B.p.flow_on)
           for (int q = 0; q < NQ; ++q) rj += (double)fpre[(size_t)q * N + j];
         rsum += rj;
-        for (int kk = 0; kk < 5; ++kk) qsum[kk] += (double)Q[(size_t)kk * N + j];
+        for (int kk = 0; kk < 5; ++kk) qsum[kk] += load_q<T>(B, j, kk);
         ++cnt;
       }
       const double rb = cnt ? rsum / cnt : B.p.rho0;
@@ -1650,7 +1904,7 @@ __global__ void __launch_bounds__(256) k_rd_apply(DevBox* __restrict__ boxes, in
         }
       }
       if (cnt)
-        for (int kk = 0; kk < 5; ++kk) Q[(size_t)kk * N + i] = T(qsum[kk] / cnt);
+        for (int kk = 0; kk < 5; ++kk) store_q_cur<T>(B, i, kk, qsum[kk] / cnt);
     }
   }
 }
@@ -1865,6 +2119,40 @@ cudaError_t launch_links(int prec, const DevBox* boxes, const int2* chunks, int 
 cudaError_t launch_colloid(DevBox* boxes, int nboxes, cudaStream_t s) {
   k_colloid<<<nboxes, 128, 0, s>>>(boxes, nboxes);
   return cudaGetLastError();
+}
+
+template <typename T, int TY>
+static cudaError_t launch_step_t(DevBox* boxes, const StepItem* items, int nitems, int zc, unsigned* sync,
+                                 double* part, int spin_limit, int commit, int* err, int grid, cudaStream_t s) {
+  k_step<T, TY><<<grid, dim3(TX, TY), 0, s>>>(boxes, items, nitems, zc, sync, part, spin_limit, commit, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step(int prec, int ty, DevBox* boxes, const StepItem* items, int nitems, int zc, unsigned* sync,
+                        double* part, int spin_limit, int commit, int* err, int grid, cudaStream_t s) {
+#define LCLB_STEP_CASE(T, Y) \
+  case Y: return launch_step_t<T, Y>(boxes, items, nitems, zc, sync, part, spin_limit, commit, err, grid, s);
+  if (prec == 0) {
+    switch (ty) { LCLB_STEP_CASE(float, 2) LCLB_STEP_CASE(float, 4) LCLB_STEP_CASE(float, 8) default: break; }
+  } else {
+    switch (ty) { LCLB_STEP_CASE(double, 2) LCLB_STEP_CASE(double, 4) LCLB_STEP_CASE(double, 8) default: break; }
+  }
+#undef LCLB_STEP_CASE
+  return cudaErrorInvalidValue;
+}
+
+int step_blocks_per_sm(int prec, int ty) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+#define LCLB_OCC(T, Y) \
+  case Y: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<T, Y>, TX * Y, 0); break;
+  if (prec == 0) {
+    switch (ty) { LCLB_OCC(float, 2) LCLB_OCC(float, 4) LCLB_OCC(float, 8) default: break; }
+  } else {
+    switch (ty) { LCLB_OCC(double, 2) LCLB_OCC(double, 4) LCLB_OCC(double, 8) default: break; }
+  }
+#undef LCLB_OCC
+  return e == cudaSuccess && n > 0 ? n : 1;
 }
 
 static inline int nblk(int N, int bs) { return (N + bs - 1) / bs; }

@@ -17,6 +17,9 @@
 
 The relaxation runs with the flow frozen (u = 0): the statics do not depend on
 it, and with the paper's constants the coupled flow at tau = 2.5 is unstable.
+It runs in FP32 storage, whose BF16 remainder of Q carries the increments
+that FP32 alone would round away, down to the 1e-8 residual; an FP64
+hand-off remains available (``tol``).
 """
 from __future__ import annotations
 
@@ -137,8 +140,9 @@ def propose(net: UNet, spec, S_target: int, torch, mode: str = "direct"):
 
 def relax_from(spec, S, q_start, tol_fp32, tol, torch, max_steps=2_000_000, check=1000):
     """Relax from q_start (None: the helix) in FP32 until tol_fp32; then, if
-    tol is given, hand the state to FP64 and continue until tol.  Returns
-    steps, wall time, residuals and the free energy."""
+    tol is given, hand the state to FP64 and continue until tol (by default
+    the FP32 storage, with the BF16 remainder of Q, goes to the 1e-8 residual
+    on its own).  Returns steps, wall time, residuals and the free energy."""
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s32 = Solver(S, S, S, precision=LC_FP32, **_params(spec))
@@ -167,7 +171,7 @@ def relax_from(spec, S, q_start, tol_fp32, tol, torch, max_steps=2_000_000, chec
     return out
 
 
-def compare(net: UNet, spec, S, torch, tol_fp32=3e-8, tol=1e-8, max_steps=2_000_000, mode="direct", plain=None):
+def compare(net: UNet, spec, S, torch, tol_fp32=1e-8, tol=None, max_steps=2_000_000, mode="direct", plain=None):
     """Relax from the helix (``plain``, when given, is a result of an earlier
     relaxation of the same case) and from the network's proposal."""
     torch.cuda.synchronize()
@@ -257,7 +261,7 @@ def main(argv=None):
     ap.add_argument("--relax-steps", type=int, default=30000)
     ap.add_argument("--epochs", type=int, default=15)
     ap.add_argument("--lr", type=float, default=2e-3)
-    ap.add_argument("--tol32", type=float, default=3e-8)
+    ap.add_argument("--tol32", type=float, default=1e-8)
     ap.add_argument("--tol64", type=float, default=None)
     ap.add_argument("--eval", type=int, default=2, help="held-out geometries compared at S")
     ap.add_argument("--big", action="store_true", help="also compare at 2S: R = 12, p = 32")

@@ -7,7 +7,10 @@ by a constant force of 1e-4; Sec. 3.1 and Eq. 9 drag law f = a v) is run
 director) and once along z (along it).  The file keeps, every 1000 steps, the
 colloid state (X, V, W, F_hyd, T_hyd, F_lc, T_lc), and at the end Q, rho and u
 at 256 seeded sample nodes, so that the GPU test can check the full-length
-run without running the oracle for 45 minutes.
+run without running the oracle for 45 minutes.  A second file,
+micro64_oracle_<pull>_fields.npz, keeps the final Q (5 components) and u at
+every node, rounded to FP32 (3e-8 relative, far inside the 1e-5 and 1e-6
+tolerances of the comparison), and the solid map.
 
     python tests/golden/make_micro64_oracle.py --pull x --threads 4
     python tests/golden/make_micro64_oracle.py --pull z --threads 4
@@ -76,7 +79,10 @@ def main():
     path = os.path.join(HERE, f"micro64_oracle_{a.pull}.json")
     with open(path, "w") as fh:
         json.dump(out, fh)
-    print(f"wrote {path} in {time.time() - t0:.0f} s")
+    fpath = os.path.join(HERE, f"micro64_oracle_{a.pull}_fields.npz")
+    np.savez_compressed(fpath, Q=o.get_Q().astype(np.float32), u=u.astype(np.float32),
+                        solid=o.get_solid().astype(np.int16), steps=np.int64(steps))
+    print(f"wrote {path} and {fpath} in {time.time() - t0:.0f} s")
 
 
 if __name__ == "__main__":

@@ -93,10 +93,18 @@ def test_init_bit_exact_fp64(P):
     assert (g.get_Q() == o.get_Q()).all()
 
 
-def test_init_rounds_to_fp32(P):
+def test_init_compensated_fp32(P):
+    """FP32 storage keeps Q as hi = RN32(Q) plus a BF16 remainder: the stored
+    value is within 2^-33 |Q| of the FP64 value (hi alone: 2^-25)."""
     L = (9, 8, 7)
     g, o = make_pair(P, L, synth.NEMATIC, P.LC_FP32, init=("uniaxial", (0, 0, 1), 1e-3, 77))
-    assert (g.get_Q() == o.get_Q().astype(np.float32).astype(np.float64)).all()
+    Qg, Qo = g.get_Q(), o.get_Q()
+    assert (np.abs(Qg - Qo) <= 2.0**-33 * np.abs(Qo)).all()
+    hi = Qo.astype(np.float32).astype(np.float64)
+    assert (np.abs(Qg - hi) <= 2.0**-24 * np.abs(Qo)).all() and (Qg != hi).any()
+    Qs = synth.random_q(L[::-1], seed=3, amp=0.3)
+    g.set_fields(P.LC_Q, Qs)
+    assert (np.abs(g.get_Q() - Qs) <= 2.0**-33 * np.abs(Qs)).all()
     p = dict(synth.NEMATIC, q0=2 * math.pi / 7)
     g2, o2 = make_pair(P, L, p, P.LC_FP64, init=("helix", 2, 1e-3, 5))
     np.testing.assert_allclose(g2.get_Q(), o2.get_Q(), atol=1e-16)
@@ -259,9 +267,10 @@ def test_lc_off_and_flow_off_switches(P):
 # ------------------------------------------------------ step variants --
 # The force + LB part of a step runs as one fused kernel, as stress/force and
 # LB kernels on two streams, or as a stored-stress kernel followed by an LB
-# kernel taking the face divergence of the stored P; the autotuner picks one
-# per box-size signature, LCLB_VARIANT forces it.
-VARIANTS = ["fused", "split", "stored"]
+# kernel taking the face divergence of the stored P; or the whole step runs
+# as one persistent launch (dataflow over z chunks of every box); the
+# autotuner picks one per box-size signature, LCLB_VARIANT forces it.
+VARIANTS = ["fused", "split", "stored", "dataflow"]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -313,6 +322,65 @@ def test_step_variants_lc_and_flow_switches(P, monkeypatch, variant):
         g.step(20)
         o.step(20)
         compare(g, o, TOL64, ncol=1, radii=[3.5])
+
+
+def test_dataflow_batch_matches_single_boxes(P, monkeypatch):
+    """Uneven boxes (periodic and walled, one chunk or many) advanced by one
+    persistent launch per step give the single-box results, which match the
+    oracle."""
+    monkeypatch.setenv("LCLB_VARIANT", "dataflow")
+    boxes = [dict(grid=(33, 21, 17), wall_z=False, params=dict(synth.NEMATIC, q0=2 * math.pi / 17)),
+             dict(grid=(16, 16, 5), wall_z=False, params=dict(synth.NEMATIC)),
+             dict(grid=(40, 12, 29), wall_z=True, params=dict(synth.NEMATIC, A0=0.05))]
+    cols = [dict(X=(16.0, 10.0, 8.0), a0=4.5, anchoring=1, w=0.02), dict(X=(7.5, 7.5, 2.2), a0=2.0),
+            dict(X=(20.2, 5.5, 14.1), a0=3.3, anchoring=0, w=0.01)]
+    B = P.Batch([dict(grid=b["grid"], wall_z=b["wall_z"], params=b["params"]) for b in boxes],
+                precision=P.LC_FP64)
+    singles = []
+    for i, (bx, c) in enumerate(zip(boxes, cols)):
+        B.boxes[i].init_uniaxial((0.1, 0.2, 1.0), amp=1e-2, seed=i)
+        B.boxes[i].add_colloid(c["X"], c["a0"], c.get("anchoring", 0), c.get("w", float("inf")))
+        s = P.Solver(*bx["grid"], wall_z=bx["wall_z"], precision=P.LC_FP64, **bx["params"])
+        s.init_uniaxial((0.1, 0.2, 1.0), amp=1e-2, seed=i)
+        s.add_colloid(c["X"], c["a0"], c.get("anchoring", 0), c.get("w", float("inf")))
+        singles.append(s)
+    assert B.step_launches() == 1
+    B.step(25)
+    for s in singles:
+        s.step(25)
+    for i, s in enumerate(singles):
+        np.testing.assert_allclose(B.boxes[i].get_Q(), s.get_Q(), atol=1e-14)
+        np.testing.assert_allclose(B.boxes[i].get_f(), s.get_f(), atol=1e-14)
+    for i in (0, 2):
+        o = oracle.Oracle(*boxes[i]["grid"], wall_z=boxes[i]["wall_z"], threads=8, **boxes[i]["params"])
+        o.init_uniaxial((0.1, 0.2, 1.0), amp=1e-2, seed=i)
+        o.add_colloid(cols[i]["X"], cols[i]["a0"], cols[i].get("anchoring", 0), cols[i].get("w", float("inf")))
+        o.step(25)
+        compare(B.boxes[i], o, TOL64, ncol=1, radii=[cols[i]["a0"]])
+
+
+def test_dataflow_wait_bound_reports_timeout(P, monkeypatch):
+    """A dependency wait of the persistent step kernel that cannot be met
+    (LCLB_TEST_STALL: the first LB item also waits on a counter nothing
+    increments) gives up after LCLB_SPIN_LIMIT polls: the call reports
+    LC_ERR_TIMEOUT and the device stays usable."""
+    monkeypatch.setenv("LCLB_VARIANT", "dataflow")
+    monkeypatch.setenv("LCLB_AUTOTUNE", "0")
+    monkeypatch.setenv("LCLB_TEST_STALL", "1")
+    monkeypatch.setenv("LCLB_SPIN_LIMIT", "2000")
+    g = P.Solver(20, 18, 16, precision=P.LC_FP32, **synth.NEMATIC)
+    g.init_uniaxial((0, 0, 1), amp=1e-3, seed=1)
+    g.step(2)
+    with pytest.raises(P.LcLbError) as e:
+        g.synchronize()
+    assert e.value.code == -6
+    monkeypatch.delenv("LCLB_TEST_STALL")
+    monkeypatch.delenv("LCLB_SPIN_LIMIT")
+    g2, o = make_pair(P, (20, 18, 16), synth.NEMATIC, P.LC_FP32, init=("uniaxial", (0, 0, 1), 1e-3, 1))
+    g2.step(5)
+    o.step(5)
+    g2.synchronize()
+    compare(g2, o, TOL32)
 
 
 def test_step_variant_override_rejects_unknown(P, monkeypatch):
