@@ -32,9 +32,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS of coupled LB+Beris–Edwards step; time-to-relaxed-defect vs plain"
 STEP_BYTES = (19 + 5) * 4 * 2  # algorithmic bytes per node of the whole coupled step (df and Q, read + write)
-# Bytes per node each kernel must move in FP32 (inputs read once, outputs written once):
-#   df 19 x 4 read + write = 152; Q 5 x 4 = 20; u 3 x 4 = 12; H 5 x 4 = 20; P 9 x 4 = 36; F 3 x 4 = 12.
-KERNEL_BYTES = {
+# Algorithmic bytes per node of each kernel: the state it must read and write
+# (df 19 x 4 read + write = 152; Q 5 x 4 read + write = 40); intermediates
+# that a design chooses to store are not counted.
+KERNEL_ALGO_BYTES = {
+    "k_step": STEP_BYTES,          # the whole step: df and Q, read + write
+    "k_flb": 152,                  # df R+W
+    "k_lb": 152,
+    "k_lbp": 152,
+    "k_force": 0,                  # stress kernels: no state written (Q is read by the Q update too)
+    "k_stress": 0,
+}
+# Bytes per node each kernel moves in this design (FP32; u 3 x 4 = 12,
+# H 5 x 4 = 20, P 9 x 4 = 36, F 3 x 4 = 12, the BF16 remainder of Q 5 x 2 = 10):
+KERNEL_DESIGN_BYTES = {
+    # df R+W; Q read by the stress and the Q update, Q written; its BF16 remainder R+W; H, P, u written and read
+    "k_step": 152 + 3 * 20 + 2 * 10 + 2 * 20 + 2 * 36 + 2 * 12,
     "k_flb": 152 + 20 + 12 + 20,   # df R+W, Q R, u W, H W
     "k_force": 20 + 12 + 20,       # Q R, F W, H W
     "k_lb": 152 + 12 + 12,         # df R+W, F R, u W
@@ -42,6 +55,8 @@ KERNEL_BYTES = {
     "k_lbp": 152 + 36 + 12,        # df R+W, P R, u W
 }
 KERNEL_DESC = {
+    "k_step": "the whole coupled step as one persistent launch (stress, LB, Q update, links, colloid; dataflow "
+              "over z chunks)",
     "k_flb": "LC stress + body force + pull collide-stream, fused",
     "k_force": "LC stress + body force (split variant)",
     "k_lb": "pull collide-stream with stored force (split variant)",
@@ -252,6 +267,34 @@ def build_batch(P, stream, seed=4, n=64):
     return B, specs
 
 
+def batch_line(steps, local):
+    """The 64-box sweep (32^3..96^3) on the same GPU: MLUPS, launches per step
+    and the whole-step roofline, for the sub-object of the bench line."""
+    import torch
+
+    import paper_1102_2193_gb300 as P
+    stream = torch.cuda.Stream(device=local)
+    B, specs = build_batch(P, stream)
+    N = sum(b["grid"][0] * b["grid"][1] * b["grid"][2] for b in specs)
+    B.step(5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    B.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    peaks = measured_peaks()
+    out = dict(workload="batched64", boxes=len(specs), nodes=N, steps=steps, value=N / (ms / 1e3) / 1e6,
+               unit="MLUPS", ms_per_step=ms, launches_per_step=B.step_launches(),
+               variant=B.profile(2)["variant"],
+               step_roofline=dict(bound="hbm", achieved=STEP_BYTES * N / (ms / 1e3) / 1e9, peak=peaks["hbm"],
+                                  unit="GB/s", frac=STEP_BYTES * N / (ms / 1e3) / 1e9 / peaks["hbm"],
+                                  bytes_per_node=STEP_BYTES))
+    B.close()
+    return out
+
+
 def run_batch(args, ws, rank, local):
     """The batched sweep: 64 uneven boxes advanced together, one graph per step."""
     import torch
@@ -330,15 +373,22 @@ def run_gpu(args, ws, rank, local):
     clocks = clk.stop()
     value = whole_job_mlups(ws, N, args.steps, ms / 1e3)
 
-    # ---- per-phase launch durations: events around each kernel on the launching stream ----
+    # ---- per-launch durations: events around each kernel on the launching stream ----
     prof = s.profile(max(10, min(200, args.steps // 5)))
     peaks = measured_peaks()
-    # the dominant kernel: the longest kernel of the force + LB part in the tuned variant
-    kname, kms = max(prof["kernels"].items(), key=lambda kv: kv[1])
-    achieved = KERNEL_BYTES[kname] * N / (kms / 1e3) / 1e9
+    # the dominant kernel: the whole-step kernel of the dataflow variant, else
+    # the longest kernel of the force + LB part of the classic variant
+    if prof["variant"] == "dataflow":
+        kname, kms = "k_step", prof["kernels"]["k_step"]
+    else:
+        kname, kms = max(prof["kernels"].items(), key=lambda kv: kv[1])
+    achieved = KERNEL_ALGO_BYTES[kname] * N / (kms / 1e3) / 1e9
+    design = KERNEL_DESIGN_BYTES[kname] * N / (kms / 1e3) / 1e9
     traffic = ncu_traffic(kname, args.workload)
-    per_kernel = {k: dict(ms=v, bytes_per_node=KERNEL_BYTES[k], gbs=KERNEL_BYTES[k] * N / (v / 1e3) / 1e9,
-                          frac=KERNEL_BYTES[k] * N / (v / 1e3) / 1e9 / peaks["hbm"])
+    per_kernel = {k: dict(ms=v, algorithmic_bytes_per_node=KERNEL_ALGO_BYTES[k],
+                          frac=KERNEL_ALGO_BYTES[k] * N / (v / 1e3) / 1e9 / peaks["hbm"],
+                          design_bytes_per_node=KERNEL_DESIGN_BYTES[k],
+                          design_frac=KERNEL_DESIGN_BYTES[k] * N / (v / 1e3) / 1e9 / peaks["hbm"])
                   for k, v in prof["kernels"].items() if v > 0}
     step_ms = ms / args.steps
     step_gbs = STEP_BYTES * N / (step_ms / 1e3) / 1e9
@@ -364,6 +414,10 @@ def run_gpu(args, ws, rank, local):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_seconds)
+    batched = None
+    if rank == 0 and ws == 1 and not args.no_batch:
+        del s
+        batched = batch_line(args.batch_steps, local)
 
     if rank == 0:
         out = dict(
@@ -378,13 +432,18 @@ def run_gpu(args, ws, rank, local):
                         l2="inputs larger than L2 (state ~0.45 GB per box); no flush", parallelism=f"replicas x{ws}"),
             roofline=dict(kernel=f"{kname} ({KERNEL_DESC[kname]})", bound="hbm",
                           achieved=achieved, peak=peaks["hbm"], unit="GB/s", frac=achieved / peaks["hbm"],
-                          traffic=traffic, bytes_per_node=KERNEL_BYTES[kname], units_per_launch=N, launch_ms=kms,
-                          peak_source=f"{peaks['src']} hbm_gbs", variant=prof["variant"], kernels=per_kernel),
+                          traffic=traffic, bytes_per_node=KERNEL_ALGO_BYTES[kname], units_per_launch=N,
+                          launch_ms=kms, peak_source=f"{peaks['src']} hbm_gbs (burst copy)",
+                          design_bytes_per_node=KERNEL_DESIGN_BYTES[kname], design_frac=design / peaks["hbm"],
+                          note="achieved = algorithmic bytes per node (df and Q, read + write, 192 B for the whole "
+                               "step; 152 B for an LB kernel) x nodes / mean event-timed launch; design_frac counts "
+                               "the intermediates this design stores",
+                          variant=prof["variant"], kernels=per_kernel),
             step_roofline=dict(bound="hbm", achieved=step_gbs, peak=peaks["hbm"], unit="GB/s",
                                frac=step_gbs / peaks["hbm"], bytes_per_node=STEP_BYTES,
                                note="whole coupled step: 192 B/node algorithmic (df + Q, read + write)"),
             phase_ms=prof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches_per_step * args.steps,
-            launches_per_step=launches_per_step, clocks=clocks)
+            launches_per_step=launches_per_step, clocks=clocks, batched64=batched)
         print(json.dumps(out), flush=True)
     if dist:
         torch.distributed.destroy_process_group()
@@ -400,6 +459,8 @@ def main():
     ap.add_argument("--workload", default="chol128_R8")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep sub-object")
+    ap.add_argument("--batch-steps", type=int, default=300)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -21,15 +21,21 @@ LC_NORMAL, LC_PLANAR = 0, 1
 LC_Q, LC_U, LC_RHO, LC_F_PRE, LC_FORCE, LC_SOLID = 0, 1, 2, 3, 4, 5
 PHASES = ("flb", "lc", "links", "colloid", "step")  # "flb": the force + LB part, whatever its variant
 
-VARIANTS = ("fused", "split", "stored")
-VARIANT_KERNELS = (("k_flb",), ("k_force", "k_lb"), ("k_stress", "k_lbp"))
+VARIANTS = ("fused", "split", "stored", "dataflow")
+VARIANT_KERNELS = (("k_flb",), ("k_force", "k_lb"), ("k_stress", "k_lbp"), ("k_stress", "k_lbp"))
 
 
 def _profile_dict(ms) -> dict:
+    """Mean ms per step: the force + LB part, the Q update, the link exchange
+    and the colloid update run as separate kernels (a breakdown), and the whole
+    step as it runs ("step": for the dataflow variant the one persistent
+    launch k_step)."""
     out = dict(zip(PHASES, ms[:5].tolist()))
     v = int(round(ms[5]))
     out["variant"] = VARIANTS[v]
     out["kernels"] = dict(zip(VARIANT_KERNELS[v], ms[6:8].tolist()))
+    if VARIANTS[v] == "dataflow":
+        out["kernels"]["k_step"] = out["step"]
     return out
 
 

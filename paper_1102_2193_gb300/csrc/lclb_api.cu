@@ -115,8 +115,17 @@ struct Group {
   // Step variant: 0 = fused stress/force/LB kernel; 1 = split: the stress/
   // force kernel and the LB kernel run concurrently in z slabs on two streams
   // (LB slab s waits for force slab s only); 2 = stored: H and P stored once
-  // per node, then the LB kernel takes the face divergence of the stored P.
+  // per node, then the LB kernel takes the face divergence of the stored P;
+  // 3 = dataflow: the whole step (stored-stress kernels, Q update, link
+  // exchange, colloid update) as one persistent launch k_step.
   int variant = 0;
+  TileCfg step_cfg{4, 8, 0};        // dataflow: tile height and depth
+  StepItem* d_items = nullptr;      // dataflow work list
+  int nitems = 0, items_cap = 0;
+  unsigned* d_sync = nullptr;       // item counter and completion counters
+  int nsync = 0, sync_cap = 0;
+  int* d_err = nullptr;             // set by k_step when a wait gave up
+  int step_grid = 0;
   int slab = 0;                              // slab thickness in z (0: whole box)
   cudaStream_t side2 = nullptr;
   std::vector<cudaEvent_t> ev_slab;
@@ -236,7 +245,7 @@ int build_chunks(Group* g) {
   std::vector<int2> ch;
   for (size_t b = 0; b < g->boxes.size(); ++b) {
     const lc_lb* h = g->boxes[b];
-    for (int s = 0; s < h->hb.nlinks_cap; s += 256) ch.push_back(make_int2((int)b, s));
+    for (int s = 0; s < h->hb.nlinks_cap; s += LINK_CHUNK) ch.push_back(make_int2((int)b, s));
   }
   if ((int)ch.size() > g->chunk_cap) {
     if (g->d_chunks) g->mem.put(g->d_chunks, g->al);
@@ -317,6 +326,10 @@ int make_box(Group* g, const lc_grid* G, const lc_params* p, lc_lb* h) {
   for (int k = 0; k < 2; ++k) {
     B.f[k] = galloc(g, NQ * N * ts);
     B.Q[k] = galloc(g, 5 * N * ts);
+    if (g->prec == LC_FP32) {
+      B.Qlo[k] = (__nv_bfloat16*)galloc(g, 5 * N * sizeof(__nv_bfloat16));
+      if (!B.Qlo[k]) return fail(&h->err, LC_ERR_OOM, "device allocation failed for a %dx%dx%d box", G->nx, G->ny, G->nz);
+    }
   }
   B.u = galloc(g, 3 * N * ts);
   B.F = galloc(g, 3 * N * ts);
@@ -330,7 +343,10 @@ int make_box(Group* g, const lc_grid* G, const lc_params* p, lc_lb* h) {
       !B.nlinks)
     return fail(&h->err, LC_ERR_OOM, "device allocation failed for a %dx%dx%d box", G->nx, G->ny, G->nz);
   cudaStream_t s = g->stream;
-  for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(B.f[k], 0, NQ * N * ts, s), &h->err);
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaMemsetAsync(B.f[k], 0, NQ * N * ts, s), &h->err);
+    if (B.Qlo[k]) CK(cudaMemsetAsync(B.Qlo[k], 0, 5 * N * sizeof(__nv_bfloat16), s), &h->err);
+  }
   CK(cudaMemsetAsync(B.u, 0, 3 * N * ts, s), &h->err);
   CK(cudaMemsetAsync(B.F, 0, 3 * N * ts, s), &h->err);
   CK(cudaMemsetAsync(B.H, 0, 5 * N * ts, s), &h->err);
@@ -380,7 +396,9 @@ Group* new_group(int prec, void* stream, int nboxes, std::string* err) {
   if (g->nsm <= 0) g->nsm = 1;
   g->d_boxes = (DevBox*)galloc(g, sizeof(DevBox) * std::max(1, nboxes));
   g->d_red = (double*)galloc(g, sizeof(double) * 64);
-  if (!g->d_boxes || !g->d_red || cudaMallocHost(&g->h_red, sizeof(double) * 64) != cudaSuccess) {
+  g->d_err = (int*)galloc(g, sizeof(int) * 4);
+  if (g->d_err) cudaMemsetAsync(g->d_err, 0, sizeof(int) * 4, g->stream);
+  if (!g->d_boxes || !g->d_red || !g->d_err || cudaMallocHost(&g->h_red, sizeof(double) * 64) != cudaSuccess) {
     fail(err, LC_ERR_OOM, "group allocation failed");
     g->mem.release(g->al);
     if (g->own_stream) cudaStreamDestroy(g->stream);
@@ -431,9 +449,9 @@ TuneKey tune_key(Group* g) {
 
 // Optional file cache (LCLB_TUNE_CACHE): one line per entry,
 // "signature precision" and NCFG triples "ty zc persistent" (fused, lc,
-// force, lb, (variant, slab, 0), stress, lb-from-stress); lines of another
-// length are skipped.
-constexpr int NCFG = 7;
+// force, lb, (variant, slab, 0), stress, lb-from-stress, dataflow step);
+// lines of another length are skipped.
+constexpr int NCFG = 8;
 void tune_file_load() {
   const char* path = getenv("LCLB_TUNE_CACHE");
   if (!path) return;
@@ -510,6 +528,12 @@ int tune_stored_fn(Group* g, void*) {
   CK(launch_phase(g, 5, 0), &g->err);
   return LC_OK;
 }
+cudaError_t launch_dataflow(Group* g, int commit);
+int build_items(Group* g);
+int tune_dataflow_fn(Group* g, void*) {
+  CK(launch_dataflow(g, 0), &g->err);
+  return LC_OK;
+}
 
 // Time every candidate tile shape of each phase kernel on the group's own
 // state (the phase kernels are idempotent between parity flips), then the
@@ -549,7 +573,13 @@ int autotune_group_inner(Group* g, std::string* desc) {
   float best_phase[NPHASE] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
   const char* venv = getenv("LCLB_TUNE_VERBOSE");
   const bool verbose = venv && venv[0] == '1';
+  // FP32 boxes: only the stored-stress kernels take the derivatives at nodes
+  // next to a solid from the compensated Q (the colloid force needs them), so
+  // the fused and split variants are not candidates there (LCLB_VARIANT still
+  // forces them)
+  const bool fp32 = g->prec == LC_FP32;
   for (int k : {3, 2, 0, 1, 4, 5}) {
+    if (fp32 && (k == 3 || k == 1)) continue;
     TileCfg best = g->ph[k].cfg;
     const std::vector<int> tys = k == 3 ? std::vector<int>{4, 6, 8} : std::vector<int>{2, 4, 8};
     const std::vector<int> zcs =
@@ -584,7 +614,7 @@ int autotune_group_inner(Group* g, std::string* desc) {
   while (l % b) l += a;
   float best_split = 1e30f;
   int best_slab = 0;
-  for (int m = 1; l * m <= maxnz; m *= 2) {
+  for (int m = 1; !fp32 && l * m <= maxnz; m *= 2) {
     g->slab = l * m;
     if ((rc = build_chunks_slab(g))) return rc;
     const float ms = time_ms(g, e0, e1, 3, tune_split_fn, nullptr, &rc);
@@ -606,16 +636,50 @@ int autotune_group_inner(Group* g, std::string* desc) {
     g->variant = 1;
     best_var = best_split;
   }
-  if (stored < best_var) g->variant = 2;
-  snprintf(buf, sizeof(buf), "split(slab=%d,%.1fus) stored(%.1fus) -> %s", best_slab, 1000.f * best_split,
-           1000.f * stored, g->variant == 0 ? "fused" : (g->variant == 1 ? "split" : "stored"));
+  if (stored < best_var || fp32) {
+    g->variant = 2;
+    best_var = stored;
+  }
+  // dataflow: the whole step as one launch, timed without committing it
+  // (against the force + LB part plus the Q update of the classic variants)
+  const float classic = best_var + best_phase[2];
+  const TileCfg lc_cfg = g->ph[2].cfg;
+  float best_df = 1e30f;
+  TileCfg best_step = g->step_cfg;
+  const char* dfenv = getenv("LCLB_DATAFLOW");
+  if (!(dfenv && dfenv[0] == '0')) {
+    for (int ty : {2, 4, 8})
+      for (int zc : {4, 8, 16}) {
+        g->step_cfg = TileCfg{ty, zc, 0};
+        if ((rc = build_items(g))) return rc;
+        const float ms = time_ms(g, e0, e1, 3, tune_dataflow_fn, nullptr, &rc);
+        if (rc) return rc;
+        if (verbose) fprintf(stderr, "lclb tune dataflow ty=%d zc=%d %.1f us\n", ty, zc, 1000.f * ms);
+        if (ms < best_df) {
+          best_df = ms;
+          best_step = g->step_cfg;
+        }
+      }
+  }
+  g->step_cfg = best_step;
+  if (best_df < classic) {
+    g->variant = 3;
+    g->ph[2].cfg = TileCfg{best_step.ty, best_step.zc, lc_cfg.persistent};
+  } else {
+    g->ph[2].cfg = lc_cfg;
+  }
+  if ((rc = build_phase(g, 2))) return rc;
+  static const char* vname[4] = {"fused", "split", "stored", "dataflow"};
+  snprintf(buf, sizeof(buf), "split(slab=%d,%.1fus) stored(%.1fus) classic+lc(%.1fus) dataflow(ty=%d,zc=%d,%.1fus) -> %s",
+           best_slab, 1000.f * best_split, 1000.f * stored, 1000.f * classic, best_step.ty, best_step.zc,
+           1000.f * best_df, vname[g->variant]);
   out += buf;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     g_tune_cache[tune_key(g)] = {g->ph[3].cfg, g->ph[2].cfg, g->ph[0].cfg, g->ph[1].cfg,
-                                 TileCfg{g->variant, g->slab, 0}, g->ph[4].cfg, g->ph[5].cfg};
+                                 TileCfg{g->variant, g->slab, 0}, g->ph[4].cfg, g->ph[5].cfg, g->step_cfg};
     tune_file_store(tune_key(g), g_tune_cache[tune_key(g)]);
   }
   g->tuned = true;
@@ -624,15 +688,22 @@ int autotune_group_inner(Group* g, std::string* desc) {
   return LC_OK;
 }
 
-// LCLB_VARIANT=fused|split|stored forces the force + LB variant of the step
+// LCLB_VARIANT=fused|split|stored|dataflow forces the variant of the step
 // (the tile shapes stay tuned); used to run every variant through the same tests.
 int apply_variant_override(Group* g) {
   const char* v = getenv("LCLB_VARIANT");
   if (!v || !v[0]) return LC_OK;
-  const int want = !strcmp(v, "fused") ? 0 : (!strcmp(v, "split") ? 1 : (!strcmp(v, "stored") ? 2 : -1));
-  if (want < 0) return fail(&g->err, LC_ERR_ARG, "LCLB_VARIANT must be fused, split or stored (got %s)", v);
+  const int want = !strcmp(v, "fused") ? 0
+                   : !strcmp(v, "split") ? 1
+                   : !strcmp(v, "stored") ? 2
+                   : !strcmp(v, "dataflow") ? 3 : -1;
+  if (want < 0) return fail(&g->err, LC_ERR_ARG, "LCLB_VARIANT must be fused, split, stored or dataflow (got %s)", v);
   if (want != g->variant) {
     g->variant = want;
+    if (want == 3) {
+      g->ph[2].cfg = TileCfg{g->step_cfg.ty, g->step_cfg.zc, g->ph[2].cfg.persistent};
+      if (int rc = build_phase(g, 2)) return rc;
+    }
     g->dirty = true;
   }
   return LC_OK;
@@ -657,11 +728,13 @@ int maybe_tune(Group* g) {
       g->slab = it->second[4].zc;
       g->ph[4].cfg = it->second[5];
       g->ph[5].cfg = it->second[6];
+      g->step_cfg = it->second[7];
       g->tuned = true;
     }
   }
   int rc = LC_OK;
   if (g->tuned) {
+    if (g->variant == 3) g->ph[2].cfg = TileCfg{g->step_cfg.ty, g->step_cfg.zc, g->ph[2].cfg.persistent};
     for (int k = 0; k < NPHASE && !rc; ++k) rc = build_phase(g, k);
     if (!rc) rc = build_chunks_slab(g);
   } else {
@@ -743,6 +816,180 @@ int enqueue_split(Group* g, int force_mode) {
   return LC_OK;
 }
 
+// ---- dataflow variant: work list of the persistent step kernel ---------------
+// Per box b with nzc = ceil(nz / zc) chunks of zc planes and tpc tiles per
+// chunk, counters (after sync[0], the item counter): stress, LB and Q update
+// done per chunk (3 nzc), then all stress, all LB, all Q update and all link
+// chunks done (4).  Chunks are visited in the order 0, nzc-1, 1, nzc-2, ...
+// for a periodic box (the wrap neighbours of the first chunks come early) and
+// 0, 1, ... between walls; at stage w a box contributes the stress tiles of
+// its w-th chunk, the LB tiles of its (w-2)-th and the Q-update tiles of its
+// (w-4)-th, its link chunks after its last LB chunk and its colloid update
+// after its last Q-update chunk.  Every item then follows what it waits for.
+int build_items(Group* g) {
+  const int ty = g->step_cfg.ty, zc = g->step_cfg.zc;
+  Phase& PL = g->ph[2];
+  if (PL.cfg.ty != ty || PL.cfg.zc != zc) {
+    PL.cfg.ty = ty;
+    PL.cfg.zc = zc;
+    if (int rc = build_phase(g, 2)) return rc;
+  }
+  const int nb = (int)g->boxes.size();
+  std::vector<int> base(nb), nzc(nb), ntx(nb), nty(nb), nlk(nb);
+  int ncnt = 1, maxz = 0;
+  for (int b = 0; b < nb; ++b) {
+    const lc_lb* h = g->boxes[b];
+    nzc[b] = (h->grid.nz + zc - 1) / zc;
+    ntx[b] = (h->grid.nx + 31) / 32;
+    nty[b] = (h->grid.ny + ty - 1) / ty;
+    nlk[b] = (h->hb.nlinks_cap + LINK_CHUNK - 1) / LINK_CHUNK;
+    base[b] = ncnt;
+    ncnt += 3 * nzc[b] + 4;
+    maxz = std::max(maxz, nzc[b]);
+  }
+  // an extra counter that nothing increments: LCLB_TEST_STALL=1 makes the
+  // first LB item wait on it (a test of the bounded waits)
+  const int never = ncnt++;
+  const char* stall_env = getenv("LCLB_TEST_STALL");
+  bool stall = stall_env && stall_env[0] == '1';
+  std::vector<StepItem> it;
+  auto chunk_of = [&](int b, int k) {
+    const int n = nzc[b];
+    if (g->boxes[b]->grid.wall_z) return k;
+    return (k % 2 == 0) ? k / 2 : n - 1 - k / 2;
+  };
+  auto blank = [](int kind, int b) {
+    StepItem I;
+    I.kind = kind;
+    I.box = b;
+    I.x0 = I.y0 = I.z0 = I.part = 0;
+    for (int k = 0; k < 4; ++k) I.wc[k] = -1, I.wt[k] = 0;
+    I.dc[0] = I.dc[1] = -1;
+    return I;
+  };
+  // counter of phase p (0 stress, 1 LB, 2 Q update) for chunk c of box b
+  auto cnt = [&](int b, int p, int c) { return base[b] + p * nzc[b] + c; };
+  auto neighbour_waits = [&](StepItem& I, int b, int p, int c) {
+    const int n = nzc[b], tpc = ntx[b] * nty[b];
+    int k = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+      int cc = c + dz;
+      if (g->boxes[b]->grid.wall_z) {
+        if (cc < 0 || cc >= n) continue;
+      } else {
+        cc = (cc + n) % n;
+      }
+      const int id = cnt(b, p, cc);
+      bool dup = false;
+      for (int j = 0; j < k; ++j) dup = dup || I.wc[j] == id;
+      if (dup) continue;
+      I.wc[k] = id;
+      I.wt[k] = tpc;
+      ++k;
+    }
+  };
+  auto tiles = [&](int kind, int b, int c) {
+    const lc_grid& G = g->boxes[b]->grid;
+    for (int yi = 0; yi < nty[b]; ++yi)
+      for (int xi = 0; xi < ntx[b]; ++xi) {
+        StepItem I = blank(kind, b);
+        I.x0 = 32 * xi;
+        I.y0 = ty * yi;
+        I.z0 = zc * c;
+        const int p = kind;  // ITEM_STRESS, ITEM_LB, ITEM_LC are 0, 1, 2
+        if (p == 1) neighbour_waits(I, b, 0, c);
+        if (p == 2) neighbour_waits(I, b, 1, c);
+        if (p == 2) I.part = PL.start[b] + (c * nty[b] + yi) * ntx[b] + xi;
+        if (p == 1 && stall) {
+          I.wc[3] = never;
+          I.wt[3] = 1;
+          stall = false;
+        }
+        I.dc[0] = cnt(b, p, c);
+        I.dc[1] = base[b] + 3 * nzc[b] + p;
+        (void)G;
+        it.push_back(I);
+      }
+  };
+  for (int w = 0; w < maxz + 4; ++w)
+    for (int b = 0; b < nb; ++b) {
+      const int n = nzc[b], tpc = ntx[b] * nty[b], all = base[b] + 3 * n;
+      if (w < n) tiles(ITEM_STRESS, b, chunk_of(b, w));
+      if (w - 2 >= 0 && w - 2 < n) {
+        tiles(ITEM_LB, b, chunk_of(b, w - 2));
+        if (w - 2 == n - 1)
+          for (int k = 0; k < nlk[b]; ++k) {
+            StepItem I = blank(ITEM_LINKS, b);
+            I.x0 = k * LINK_CHUNK;
+            I.wc[0] = all + 1;
+            I.wt[0] = n * tpc;
+            I.dc[0] = all + 3;
+            it.push_back(I);
+          }
+      }
+      if (w - 4 >= 0 && w - 4 < n) {
+        tiles(ITEM_LC, b, chunk_of(b, w - 4));
+        if (w - 4 == n - 1) {
+          StepItem I = blank(ITEM_COLLOID, b);
+          for (int k = 0; k < 3; ++k) {
+            I.wc[k] = all + k;
+            I.wt[k] = n * tpc;
+          }
+          if (nlk[b] > 0) {
+            I.wc[3] = all + 3;
+            I.wt[3] = nlk[b];
+          }
+          it.push_back(I);
+        }
+      }
+    }
+  if ((int)it.size() > g->items_cap) {
+    if (g->d_items) g->mem.put(g->d_items, g->al);
+    g->items_cap = (int)it.size() + 256;
+    g->d_items = (StepItem*)galloc(g, sizeof(StepItem) * g->items_cap);
+    if (!g->d_items) return fail(&g->err, LC_ERR_OOM, "step item list allocation failed");
+  }
+  if (ncnt > g->sync_cap) {
+    if (g->d_sync) g->mem.put(g->d_sync, g->al);
+    g->sync_cap = ncnt + 64;
+    g->d_sync = (unsigned*)galloc(g, sizeof(unsigned) * g->sync_cap);
+    if (!g->d_sync) return fail(&g->err, LC_ERR_OOM, "step counter allocation failed");
+  }
+  g->nitems = (int)it.size();
+  g->nsync = ncnt;
+  CK(cudaMemcpyAsync(g->d_items, it.data(), sizeof(StepItem) * it.size(), cudaMemcpyHostToDevice, g->stream),
+     &g->err);
+  g->step_grid = g->nsm * step_blocks_per_sm(g->prec, ty);
+  return LC_OK;
+}
+
+// Polls of a dependency wait before k_step gives up (about a second);
+// LCLB_SPIN_LIMIT overrides it.
+int spin_limit() {
+  const char* e = getenv("LCLB_SPIN_LIMIT");
+  if (e && e[0]) return std::max(0, atoi(e));
+  return 1 << 23;
+}
+
+cudaError_t launch_dataflow(Group* g, int commit) {
+  cudaError_t e = cudaMemsetAsync(g->d_sync, 0, sizeof(unsigned) * g->nsync, g->stream);
+  if (e != cudaSuccess) return e;
+  return launch_step(g->prec, g->step_cfg.ty, g->d_boxes, g->d_items, g->nitems, g->step_cfg.zc, g->d_sync,
+                     g->ph[2].d_part, spin_limit(), commit, g->d_err, g->step_grid, g->stream);
+}
+
+// A wait of k_step that gave up leaves *d_err set: report it (and clear it).
+int check_step_err(Group* g, std::string* err) {
+  if (g->variant != 3) return LC_OK;
+  int* hv = reinterpret_cast<int*>(g->h_red + 63);
+  CK(cudaMemcpyAsync(hv, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream), err);
+  CK(cudaStreamSynchronize(g->stream), err);
+  if (*hv == 0) return LC_OK;
+  CK(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream), err);
+  CK(cudaStreamSynchronize(g->stream), err);
+  return fail(err, LC_ERR_TIMEOUT, "a dependency wait of the persistent step kernel gave up; the state is invalid");
+}
+
 // One coupled step: fused stress + body force + collide/stream, then the Q
 // update on the main stream and the link momentum exchange on the side
 // stream (both read only what the fused kernel wrote), joined before the
@@ -759,6 +1006,13 @@ int enqueue_force_lb(Group* g) {
 }
 
 int enqueue_step(Group* g) {
+  if (g->variant == 3) {
+    CK(launch_dataflow(g, 1), &g->err);
+    if (g->nmob > 0)
+      CK(launch_rediscretise(g->prec, g->d_boxes, (int)g->boxes.size(), g->d_mob, g->nmob, g->nsm, g->stream),
+         &g->err);
+    return LC_OK;
+  }
   if (int rc = enqueue_force_lb(g)) return rc;
   if (g->nchunks > 0) {
     CK(cudaEventRecord(g->ev_fork, g->stream), &g->err);
@@ -818,6 +1072,8 @@ int capture(Group* g) {
     cudaGraphDestroy(g->graph);
     g->graph = nullptr;
   }
+  if (g->variant == 3)
+    if (int rc = build_items(g)) return rc;
   CK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal), &g->err);
   int rc = enqueue_step(g);
   cudaGraph_t gr = nullptr;
@@ -885,8 +1141,25 @@ int group_profile(Group* g, int n, double* ms) {
     cudaEventElapsedTime(&t, ev[0], ev[5]);
     acc[5] += t;
   }
-  for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
   for (int k = 0; k < 5; ++k) ms[k] = acc[k] / n;
+  if (g->variant == 3) {
+    // the step as it runs: one persistent launch (whole-step time in ms[4])
+    if (g->dirty && (rc = build_items(g))) return rc;
+    CK(cudaEventRecord(ev[0], g->stream), &g->err);
+    for (int s = 0; s < n; ++s) {
+      CK(launch_dataflow(g, 1), &g->err);
+      if (g->nmob > 0)
+        CK(launch_rediscretise(g->prec, g->d_boxes, (int)g->boxes.size(), g->d_mob, g->nmob, g->nsm, g->stream),
+           &g->err);
+    }
+    CK(cudaEventRecord(ev[4], g->stream), &g->err);
+    CK(cudaEventSynchronize(ev[4]), &g->err);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ev[0], ev[4]);
+    ms[4] = t / n;
+    if ((rc = check_step_err(g, &g->err))) return rc;
+  }
+  for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
   ms[5] = g->variant;
   ms[6] = acc[5] / n;
   ms[7] = k2 >= 0 ? (acc[0] - acc[5]) / n : 0.0;
@@ -900,6 +1173,10 @@ int group_step(Group* g, int n) {
   if (rc) return rc;
   const char* env = getenv("LCLB_NO_GRAPH");
   if (env && env[0] == '1') {
+    if (g->variant == 3 && g->dirty) {
+      if ((rc = build_items(g))) return rc;
+      g->dirty = false;
+    }
     for (int s = 0; s < n; ++s)
       if ((rc = enqueue_step(g))) return rc;
     return LC_OK;
@@ -916,6 +1193,7 @@ int box_residual(Group* g, int b, double* rms, double* mx, long long nfluid) {
   CK(cudaMemcpyAsync(g->h_red, g->d_red, 2 * sizeof(double), cudaMemcpyDeviceToHost, g->stream), &g->err);
   CK(cudaStreamSynchronize(g->stream), &g->err);
   *rms = nfluid > 0 ? std::sqrt(g->h_red[0] / (double)nfluid) : 0.0;
+  if (int rc = check_step_err(g, &g->err)) return rc;
   *mx = g->h_red[1];
   return LC_OK;
 }
@@ -1168,7 +1446,7 @@ int lc_lb_step(lc_lb* h, int nsteps) {
 int lc_lb_synchronize(lc_lb* h) {
   if (int rc = h_check(h)) return rc;
   CK(cudaStreamSynchronize(h->g->stream), &h->err);
-  return LC_OK;
+  return check_step_err(h->g, &h->err);
 }
 
 int lc_lb_relax(lc_lb* h, double tol, long long max_steps, int check_every, long long* steps_out, double* resid_out) {
@@ -1227,7 +1505,7 @@ int lc_lb_get_fields(lc_lb* h, int which, void* dst, size_t bytes, int dst_is_de
                      dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream),
      &h->err);
   CK(cudaStreamSynchronize(g->stream), &h->err);
-  return LC_OK;
+  return check_step_err(g, &h->err);
 }
 
 int lc_lb_get_colloid(lc_lb* h, int id, double out[27]) {
@@ -1236,6 +1514,7 @@ int lc_lb_get_colloid(lc_lb* h, int id, double out[27]) {
   DevColloid C;
   CK(cudaMemcpyAsync(&C, h->hb.col + id, sizeof(C), cudaMemcpyDeviceToHost, h->g->stream), &h->err);
   CK(cudaStreamSynchronize(h->g->stream), &h->err);
+  if (int rc = check_step_err(h->g, &h->err)) return rc;
   const double* src[9] = {C.X, C.V, C.W, C.Fh, C.Th, C.Flc, C.Tlc, C.imp, C.aimp};
   for (int k = 0; k < 9; ++k)
     for (int a = 0; a < 3; ++a) out[3 * k + a] = src[k][a];

@@ -13,6 +13,21 @@ constexpr int FORCE_FE = 2;   // write free-energy partials (one double per tile
 constexpr int LB_MOM = 1;     // write mass/momentum partials (4 doubles per tile)
 constexpr int LC_RESID = 1;   // write residual partials (sum of squares, max; 2 doubles per tile)
 
+// boundary links per link-exchange work unit
+constexpr int LINK_CHUNK = 256;
+
+// One work item of the persistent step kernel k_step: a tile (32 x ty x zc)
+// of one phase of one box, a chunk of a box's boundary links, or a box's
+// colloid update.  Before it runs, every counter wc[k] >= 0 must have
+// reached wt[k]; when it is done, the counters dc[0], dc[1] (>= 0) are
+// incremented.  part: index of the tile's residual partials (LC items).
+enum { ITEM_STRESS = 0, ITEM_LB = 1, ITEM_LC = 2, ITEM_LINKS = 3, ITEM_COLLOID = 4 };
+struct StepItem {
+  int kind, box, x0, y0, z0, part;
+  int wc[4], wt[4];
+  int dc[2];
+};
+
 // export selectors (same values as LC_* in lc_lb.h)
 constexpr int EXP_Q = 0, EXP_U = 1, EXP_RHO = 2, EXP_F = 3, EXP_FORCE = 4, EXP_SOLID = 5;
 
@@ -35,6 +50,15 @@ cudaError_t launch_stress(int prec, const Launch& L, int mode, double* part);  /
 cudaError_t launch_lbp(int prec, const Launch& L, int mode, double* part);     // LB with the force from stored P
 cudaError_t launch_links(int prec, const DevBox* boxes, const int2* chunks, int nchunks, int grid, cudaStream_t s);
 cudaError_t launch_colloid(DevBox* boxes, int nboxes, cudaStream_t s);
+// One coupled step (stress, LB, Q update, link exchange, colloid update of
+// every box) as one persistent launch over the item list; sync holds the
+// item counter (sync[0]) and the completion counters, zeroed before each
+// launch.  commit = 0 leaves the state as it was (the colloid items only
+// clear their sums): a timing run.  A wait that exceeds spin_limit polls
+// sets *err and the item is skipped.
+cudaError_t launch_step(int prec, int ty, DevBox* boxes, const StepItem* items, int nitems, int zc, unsigned* sync,
+                        double* part, int spin_limit, int commit, int* err, int grid, cudaStream_t s);
+int step_blocks_per_sm(int prec, int ty);
 // Re-discretisation after the colloid update; mob lists (box, colloid) of mobile colloids.
 cudaError_t launch_rediscretise(int prec, DevBox* boxes, int nboxes, const int2* mob, int nmob, int nsm,
                                 cudaStream_t s);
