@@ -146,6 +146,7 @@ struct Group {
   bool dirty = true, tuned = false;
   int graph_kernels = 0;  // kernel nodes of the captured step
   int nsm = 0;
+  int dev = 0;            // the device current when the group was created
   std::string err;
 };
 
@@ -182,6 +183,10 @@ double bulk_q(double gam) {
 
 void* galloc(Group* g, size_t bytes) { return g->mem.get(bytes, g->stream, g->al); }
 
+// Tile width in x of phase k for box b: 64 for the two-node paths of the
+// stored-stress kernel and of the Q update (FP32 boxes of even width), else 32.
+int tile_width(Group* g, int k, int b) { return ((k == 2 || k == 4) && g->boxes[b]->hb.pair) ? 64 : 32; }
+
 // Tile list of one phase for every box of the group.
 int build_phase(Group* g, int k) {
   Phase& P = g->ph[k];
@@ -190,10 +195,11 @@ int build_phase(Group* g, int k) {
   P.count.assign(g->boxes.size(), 0);
   for (size_t b = 0; b < g->boxes.size(); ++b) {
     const lc_grid& G = g->boxes[b]->grid;
+    const int xs = tile_width(g, k, (int)b);
     P.start[b] = (int)tl.size();
     for (int z = 0; z < G.nz; z += P.cfg.zc)
       for (int y = 0; y < G.ny; y += P.cfg.ty)
-        for (int x = 0; x < G.nx; x += 32) tl.push_back(make_int4((int)b, x, y, z));
+        for (int x = 0; x < G.nx; x += xs) tl.push_back(make_int4((int)b, x, y, z));
     P.count[b] = (int)tl.size() - P.start[b];
   }
   if (P.d_tiles) g->mem.put(P.d_tiles, g->al);
@@ -314,6 +320,7 @@ int make_box(Group* g, const lc_grid* G, const lc_params* p, lc_lb* h) {
   DevBox& B = h->hb;
   memset(&B, 0, sizeof(B));
   B.nx = G->nx; B.ny = G->ny; B.nz = G->nz; B.wall_z = G->wall_z ? 1 : 0;
+  B.pair = pair_width(G->nx, g->prec == LC_FP32) ? 1 : 0;
   B.N = G->nx * G->ny * G->nz;
   const size_t N = (size_t)B.N, ts = tsize(g->prec);
   B.p.rho0 = p->rho0; B.p.tau = p->tau; B.p.A0 = p->A0; B.p.gamma = p->gamma; B.p.K = p->K; B.p.q0 = p->q0;
@@ -392,6 +399,7 @@ Group* new_group(int prec, void* stream, int nboxes, std::string* err) {
   }
   int dev = 0;
   cudaGetDevice(&dev);
+  g->dev = dev;
   cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, dev);
   if (g->nsm <= 0) g->nsm = 1;
   g->d_boxes = (DevBox*)galloc(g, sizeof(DevBox) * std::max(1, nboxes));
@@ -835,12 +843,16 @@ int build_items(Group* g) {
     if (int rc = build_phase(g, 2)) return rc;
   }
   const int nb = (int)g->boxes.size();
-  std::vector<int> base(nb), nzc(nb), ntx(nb), nty(nb), nlk(nb);
+  // tiles per chunk row in x: stress (ntxs), LB (ntxl, always 32 wide), Q update (ntx)
+  std::vector<int> base(nb), nzc(nb), ntx(nb), ntxs(nb), ntxl(nb), nty(nb), nlk(nb);
   int ncnt = 1, maxz = 0;
   for (int b = 0; b < nb; ++b) {
     const lc_lb* h = g->boxes[b];
     nzc[b] = (h->grid.nz + zc - 1) / zc;
-    ntx[b] = (h->grid.nx + 31) / 32;
+    const int ws = tile_width(g, 4, b), wq = tile_width(g, 2, b);
+    ntxs[b] = (h->grid.nx + ws - 1) / ws;
+    ntxl[b] = (h->grid.nx + 31) / 32;
+    ntx[b] = (h->grid.nx + wq - 1) / wq;
     nty[b] = (h->grid.ny + ty - 1) / ty;
     nlk[b] = (h->hb.nlinks_cap + LINK_CHUNK - 1) / LINK_CHUNK;
     base[b] = ncnt;
@@ -870,7 +882,7 @@ int build_items(Group* g) {
   // counter of phase p (0 stress, 1 LB, 2 Q update) for chunk c of box b
   auto cnt = [&](int b, int p, int c) { return base[b] + p * nzc[b] + c; };
   auto neighbour_waits = [&](StepItem& I, int b, int p, int c) {
-    const int n = nzc[b], tpc = ntx[b] * nty[b];
+    const int n = nzc[b], tpc = (p == 0 ? ntxs[b] : (p == 1 ? ntxl[b] : ntx[b])) * nty[b];
     int k = 0;
     for (int dz = -1; dz <= 1; ++dz) {
       int cc = c + dz;
@@ -890,10 +902,12 @@ int build_items(Group* g) {
   };
   auto tiles = [&](int kind, int b, int c) {
     const lc_grid& G = g->boxes[b]->grid;
+    const int nxt = kind == ITEM_STRESS ? ntxs[b] : (kind == ITEM_LB ? ntxl[b] : ntx[b]);
+    const int ws = kind == ITEM_STRESS ? tile_width(g, 4, b) : (kind == ITEM_LB ? 32 : tile_width(g, 2, b));
     for (int yi = 0; yi < nty[b]; ++yi)
-      for (int xi = 0; xi < ntx[b]; ++xi) {
+      for (int xi = 0; xi < nxt; ++xi) {
         StepItem I = blank(kind, b);
-        I.x0 = 32 * xi;
+        I.x0 = ws * xi;
         I.y0 = ty * yi;
         I.z0 = zc * c;
         const int p = kind;  // ITEM_STRESS, ITEM_LB, ITEM_LC are 0, 1, 2
@@ -913,7 +927,8 @@ int build_items(Group* g) {
   };
   for (int w = 0; w < maxz + 4; ++w)
     for (int b = 0; b < nb; ++b) {
-      const int n = nzc[b], tpc = ntx[b] * nty[b], all = base[b] + 3 * n;
+      const int n = nzc[b], tpc = ntx[b] * nty[b], tpcs = ntxs[b] * nty[b], tpcl = ntxl[b] * nty[b],
+                all = base[b] + 3 * n;
       if (w < n) tiles(ITEM_STRESS, b, chunk_of(b, w));
       if (w - 2 >= 0 && w - 2 < n) {
         tiles(ITEM_LB, b, chunk_of(b, w - 2));
@@ -922,7 +937,7 @@ int build_items(Group* g) {
             StepItem I = blank(ITEM_LINKS, b);
             I.x0 = k * LINK_CHUNK;
             I.wc[0] = all + 1;
-            I.wt[0] = n * tpc;
+            I.wt[0] = n * tpcl;
             I.dc[0] = all + 3;
             it.push_back(I);
           }
@@ -933,7 +948,7 @@ int build_items(Group* g) {
           StepItem I = blank(ITEM_COLLOID, b);
           for (int k = 0; k < 3; ++k) {
             I.wc[k] = all + k;
-            I.wt[k] = n * tpc;
+            I.wt[k] = n * (k == 0 ? tpcs : (k == 1 ? tpcl : tpc));
           }
           if (nlk[b] > 0) {
             I.wc[3] = all + 3;
@@ -1385,6 +1400,7 @@ int lc_lb_add_colloid(lc_lb* h, const double X[3], double a0, int anchoring, dou
   C.a0 = a0;
   C.w = w;
   C.strong = (!(w > 0.0) || std::isinf(w)) ? 1 : 0;
+  C.wfac = C.strong ? 1.0 : w / (h->hb.p.K + w);
   C.anchoring = anchoring;
   C.mobile = mobile ? 1 : 0;
   C.M = h->params.rho0 * 4.0 / 3.0 * M_PI * a0 * a0 * a0;
@@ -1764,10 +1780,13 @@ double* g_noalloc_ptr[128] = {nullptr};
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_BLOCKS * 6 + 8];
 
 // Device address of the scratch on the current device, looked up once per
-// device (the host symbol is only a stand-in, not a device address).
-static int noalloc_scratch(double** out, std::string* err) {
+// device (the host symbol is only a stand-in, not a device address) in the
+// device's primary context.  The current device must be the group's.
+static int noalloc_scratch(const Group* g, double** out, std::string* err) {
   int dev = 0;
   CK(cudaGetDevice(&dev), err);
+  if (dev != g->dev)
+    return fail(err, LC_ERR_ARG, "current device %d is not the handle's device %d", dev, g->dev);
   if (dev < 0 || dev >= 128) return fail(err, LC_ERR_ARG, "device index %d out of range", dev);
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
@@ -1792,7 +1811,7 @@ int lc_lb_diagnostics_noalloc(lc_lb* h, lc_diag* out) {
                 "box of %d nodes exceeds the %d-node limit of the allocation-free diagnostics", h->hb.N,
                 NOALLOC_MAX_BLOCKS * 256);
   double* scr = nullptr;
-  int rc = noalloc_scratch(&scr, &h->err);
+  int rc = noalloc_scratch(h->g, &scr, &h->err);
   if (rc) return rc;
   Group* g = h->g;
   CK(launch_diag_state(g->prec, g->d_boxes, h->index, h->hb.N, scr, g->stream), &h->err);

@@ -57,6 +57,7 @@ struct DevColloid {
   double a0, w, M, I;
   double Fext[3];
   int anchoring, mobile, strong, pad;
+  double wfac;     // weight of Q0 in the surface value: w / (K + w), 1 for strong anchoring
   double acc[24];  // step sums: F_hyd, T_hyd, F_lc, T_lc, then the link drag tensors zv, zw (6 each, xx xy xz yy yz zz)
   double Fh[3], Th[3], Flc[3], Tlc[3];
   double imp[3], aimp[3];
@@ -77,6 +78,7 @@ struct DevState {
 
 struct DevBox {
   int nx, ny, nz, wall_z;
+  int pair, pad0;       // 1: FP32 box of even width (two-node paths of the stress kernel and the Q update)
   int N, ncol;
   int nlinks_cap, chg_cap;
   int* chg;             // change list: (node, colloid << 1 | uncovered) pairs
@@ -101,6 +103,11 @@ struct DevBox {
   PhysT<float> pf;
   PhysT<double> pd;
 };
+
+// FP32 boxes of even width run the two-node paths of the stress kernel and
+// the Q update over tiles 64 nodes wide (those phases' tile lists step x by 64).
+__host__ __device__ __forceinline__ bool pair_width(int nx, bool fp32) { return fp32 && nx % 2 == 0; }
+__device__ __forceinline__ bool pair_box(const DevBox& B) { return B.pair != 0; }
 
 template <typename T>
 __device__ __forceinline__ const PhysT<T>& phys(const DevBox& B);
@@ -444,14 +451,66 @@ __device__ __forceinline__ void gather_q(const DevBox& B, const T* __restrict__ 
   }
 }
 
+// 1/sqrt(v) in FP64 from the FP32 estimate and one Newton step (relative
+// error ~1e-14 for the unit vectors of the surface values).
+__device__ __forceinline__ double rsqrt_f64(double v) {
+  double r = (double)rsqrtf((float)v);
+  return r * (1.5 - 0.5 * v * r * r);
+}
+
+// Surface order Q0 (Eq. 7) for the nodes next to a solid in FP32 storage, in
+// FP64: the unit normal s at solid node (sx, sy, sz) of colloid c (c < 0: a z
+// wall, n0 = z); homeotropic n0 = s, planar n0 = nf projected on the plane
+// normal to s (nf: the node's director, computed once per node), the
+// tie-break s x e_k as surface_q0.
+__device__ __forceinline__ void surface_q0_near(const DevBox& B, int c, int sx, int sy, int sz, const double nf[3],
+                                                double q0[5]) {
+  double n[3];
+  if (c < 0) {
+    n[0] = 0.0; n[1] = 0.0; n[2] = 1.0;
+  } else {
+    const DevColloid& C = B.col[c];
+    double d[3];
+    disp(B, (double)sx, (double)sy, (double)sz, C.X, d);
+    const double ri = rsqrt_f64(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const double sv[3] = {d[0] * ri, d[1] * ri, d[2] * ri};
+    if (C.anchoring == 0) {
+      n[0] = sv[0]; n[1] = sv[1]; n[2] = sv[2];
+    } else {
+      const double ns = nf[0] * sv[0] + nf[1] * sv[1] + nf[2] * sv[2];
+      double pv[3] = {nf[0] - ns * sv[0], nf[1] - ns * sv[1], nf[2] - ns * sv[2]};
+      double p2 = pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2];
+      if (p2 < 1e-24) {  // director along the normal: tangent s x e_k, k least aligned with s
+        int k = 0;
+        if (fabs(sv[1]) < fabs(sv[k])) k = 1;
+        if (fabs(sv[2]) < fabs(sv[k])) k = 2;
+        double e[3] = {0.0, 0.0, 0.0};
+        e[k] = 1.0;
+        pv[0] = sv[1] * e[2] - sv[2] * e[1];
+        pv[1] = sv[2] * e[0] - sv[0] * e[2];
+        pv[2] = sv[0] * e[1] - sv[1] * e[0];
+        p2 = pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2];
+      }
+      const double pi = rsqrt_f64(p2);
+      n[0] = pv[0] * pi; n[1] = pv[1] * pi; n[2] = pv[2] * pi;
+    }
+  }
+  const double S0 = B.pd.S0, third = 1.0 / 3.0;
+  q0[0] = S0 * (n[0] * n[0] - third);
+  q0[1] = S0 * n[0] * n[1];
+  q0[2] = S0 * n[0] * n[2];
+  q0[3] = S0 * (n[1] * n[1] - third);
+  q0[4] = S0 * n[1] * n[2];
+}
+
 // FP32 storage, node next to a solid or wall: the derivatives from the
 // compensated values hi + lo of the node and of its face neighbours, each
 // neighbour difference formed as (hi_j - hi_i) + (lo_j - lo_i), and a solid
 // or wall neighbour's surface value as Q0 - Q_i scaled by w/(K + w) (1 for
-// strong anchoring), with Q0 and that difference in FP64.  With hi alone the rounding of Q (~3e-8) enters the
-// Laplacian of every node at the colloid surface, and the colloid's LC force,
-// a small sum of large face terms, would carry it at ~1e-4 relative.
-// qi receives the node's Q (hi + lo in FP32).
+// strong anchoring), with Q0 and that difference in FP64.  With hi alone the
+// rounding of Q (~3e-8) enters the Laplacian of every node at the colloid
+// surface, and the colloid's LC force, a small sum of large face terms, would
+// carry it at ~1e-4 relative.  qi receives the node's Q (hi + lo in FP32).
 __device__ __forceinline__ void near_derivatives_f32(const DevBox& B, int x, int y, int z, int i, float qi[5],
                                                      float dq[3][5], float lap[5]) {
   const int N = B.N, qpar = B.st->qpar;
@@ -464,21 +523,28 @@ __device__ __forceinline__ void near_derivatives_f32(const DevBox& B, int x, int
     ql[k] = __bfloat162float(Lo[(size_t)k * N + i]);
     qi[k] = qh[k] + ql[k];
   }
-  int nb[6], zz[2];
+  int nb[6], zz[2], cf[6];
   face_neighbours(B, x, y, z, nb, zz);
   const int nx = B.nx, ny = B.ny;
+  bool planar = false;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const int j = nb[d];
+    cf[d] = j < 0 ? -1 : (int)(B.mask[j] & IDMASK) - 1;  // colloid of a solid neighbour, else -1
+    if (cf[d] >= 0 && B.col[cf[d]].anchoring != 0) planar = true;
+  }
+  double nf[3] = {1.0, 0.0, 0.0};
+  if (planar) {
+    double qid[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) qid[k] = (double)qh[k] + (double)ql[k];
+    principal_dir<double>(qid, nf);
+  }
   float dn[6][5];
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     const int j = nb[d];
-    int c = -1;
-    bool solid = true;
-    if (j >= 0) {
-      const uint8_t mj = B.mask[j] & IDMASK;
-      solid = mj != 0;
-      c = (int)mj - 1;
-    }
-    if (!solid) {
+    if (j >= 0 && cf[d] < 0) {
 #pragma unroll
       for (int k = 0; k < 5; ++k)
         dn[d][k] = (__ldg(Q + (size_t)k * N + j) - qh[k]) + (__bfloat162float(Lo[(size_t)k * N + j]) - ql[k]);
@@ -490,15 +556,10 @@ __device__ __forceinline__ void near_derivatives_f32(const DevBox& B, int x, int
       if (d == 3) sy = y == 0 ? ny - 1 : y - 1;
       if (d == 4) sz = zz[0];
       if (d == 5) sz = zz[1];
-      // the surface value in FP64: its normal (and for planar anchoring the
-      // director of Q) enter the face term at the same order as the rounding
-      // this path avoids
-      double qid[5], q0[5];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) qid[k] = (double)qh[k] + (double)ql[k];
-      surface_q0<double>(B, c, sx, sy, sz, qid, q0);
-      const bool strong = (c < 0) || B.col[c].strong;
-      const double s = strong ? 1.0 : B.col[c].w / (B.pd.K + B.col[c].w);
+      const int c = j < 0 ? -1 : cf[d];
+      double q0[5];
+      surface_q0_near(B, c, sx, sy, sz, nf, q0);
+      const double s = c < 0 ? 1.0 : B.col[c].wfac;
 #pragma unroll
       for (int k = 0; k < 5; ++k) dn[d][k] = (float)(s * ((q0[k] - (double)qh[k]) - (double)ql[k]));
     }
@@ -632,8 +693,13 @@ __device__ __forceinline__ void stress(const PhysT<T>& P, const T q[5], const T 
 //   P   = f' I + 2 xi (Q + I/3) Q:H - xi (A + A^T) - (2 xi/3) H - E + A - A^T,
 //         A = Q H,  E_ab = K <d_a Q, d_b Q> + 2 K q0 sum_gn d_a Q_gn eps_mbg Q_mn  (Eq. 4)
 // The same expressions as molecular_field / free_energy_density / stress.
-template <typename T, bool NEED_P>
-__device__ __forceinline__ void lc_node_d(const PhysT<T>& P, const T qi[5], const T dq[3][5], const T lap[5], T h[5],
+// lc_node_d: the same from the derivatives dq[g][k] = d_g Q_k and the
+// Laplacian lap[k].  T is the arithmetic type of the node values (float,
+// double, or f2: two nodes at once); C that of the constants (float for f2).
+// Every constant factor is formed in C first, so that for f2 each term is one
+// packed multiply or fused multiply-add.
+template <typename T, bool NEED_P, typename C>
+__device__ __forceinline__ void lc_node_d(const PhysT<C>& P, const T qi[5], const T dq[3][5], const T lap[5], T h[5],
                                           T p[9], T* fprime);
 
 template <typename T, bool NEED_P>
@@ -641,15 +707,19 @@ __device__ __forceinline__ void lc_node(const PhysT<T>& P, const T qi[5], const 
                                         T* fprime) {
   T dq[3][5], lap[5];
   derivatives(qi, qn, dq, lap);
-  lc_node_d<T, NEED_P>(P, qi, dq, lap, h, p, fprime);
+  lc_node_d<T, NEED_P, T>(P, qi, dq, lap, h, p, fprime);
 }
 
-// The same from the derivatives dq[g][k] = d_g Q_k and the Laplacian lap[k].
-template <typename T, bool NEED_P>
-__device__ __forceinline__ void lc_node_d(const PhysT<T>& P, const T qi[5], const T dq[3][5], const T lap[5], T h[5],
+template <typename T, bool NEED_P, typename C>
+__device__ __forceinline__ void lc_node_d(const PhysT<C>& P, const T qi[5], const T dq[3][5], const T lap[5], T h[5],
                                           T p[9], T* fprime) {
-  const T A0 = P.A0, g = P.gamma, K = P.K, q0 = P.q0;
-  T Q[3][3], D[3][3][3], S2[3][3], C[3][3];
+  const C A0 = P.A0, g = P.gamma, K = P.K, q0 = P.q0, xi = P.xi;
+  const C third = C(1) / C(3);
+  const C A0g = A0 * g, twoKq0 = C(2) * K * q0;
+  const C c_lin = -A0 * (C(1) - g * third) - C(4) * K * q0 * q0;  // H: coefficient of Q beyond -A0 g Tr(Q^2)
+  const C A0g3 = A0g * third;
+  // Q (3x3), D[g] = d_g Q (3x3 each) from the 5 stored components
+  T Q[3][3], D[3][3][3], S2[3][3], Cm[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -668,18 +738,19 @@ __device__ __forceinline__ void lc_node_d(const PhysT<T>& P, const T qi[5], cons
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) C[a][b] = D[(a + 1) % 3][(a + 2) % 3][b] - D[(a + 2) % 3][(a + 1) % 3][b];
+    for (int b = 0; b < 3; ++b) Cm[a][b] = D[(a + 1) % 3][(a + 2) % 3][b] - D[(a + 2) % 3][(a + 1) % 3][b];
   const T trq2 = S2[0][0] + S2[1][1] + S2[2][2];
-  const T cb = -A0 * (T(1) - g / T(3)) - A0 * g * trq2 - T(4) * K * q0 * q0;
-  const T A0g = A0 * g, twoKq0 = T(2) * K * q0;
+  const T cb = c_lin - A0g * trq2;
+  const T tq3 = A0g3 * trq2;
   T H[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = a; b < 3; ++b) {
       const int k = a == 0 ? b : (a == 1 ? 2 + b : 5);
-      const T lp = k < 5 ? lap[k] : -lap[0] - lap[3];
-      T v = cb * Q[a][b] + A0g * (S2[a][b] - (a == b ? trq2 / T(3) : T(0))) + K * lp - twoKq0 * (C[a][b] + C[b][a]);
+      const T lp = k < 5 ? lap[k] : -(lap[0] + lap[3]);
+      T v = cb * Q[a][b] + A0g * S2[a][b] + K * lp - twoKq0 * (Cm[a][b] + Cm[b][a]);
+      if (a == b) v = v - tq3;
       H[a][b] = v;
       H[b][a] = v;
     }
@@ -692,54 +763,55 @@ __device__ __forceinline__ void lc_node_d(const PhysT<T>& P, const T qi[5], cons
   T E[3][3], tz[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) tz[a] = dq[a][0] + dq[a][3];
+  const C twoK = C(2) * K;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = a; b < 3; ++b) {
-      const T e = dq[a][0] * dq[b][0] + dq[a][3] * dq[b][3] + tz[a] * tz[b] +
-                  T(2) * (dq[a][1] * dq[b][1] + dq[a][2] * dq[b][2] + dq[a][4] * dq[b][4]);
-      E[a][b] = K * e;
-      E[b][a] = K * e;
+      const T e = K * (dq[a][0] * dq[b][0] + dq[a][3] * dq[b][3] + tz[a] * tz[b]) +
+                  twoK * (dq[a][1] * dq[b][1] + dq[a][2] * dq[b][2] + dq[a][4] * dq[b][4]);
+      E[a][b] = e;
+      E[b][a] = e;
     }
   const T Kgrad2 = E[0][0] + E[1][1] + E[2][2];  // K |grad Q|^2
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      T e2 = T(0);
-#pragma unroll
-      for (int gg = 0; gg < 3; ++gg) {
-        if (gg == b) continue;
-        const int m = 3 - b - gg;
-        const T sgn = ((m - b + 3) % 3 == 2) ? T(1) : T(-1);  // eps(m, b, gg)
-        e2 += sgn * (D[a][gg][0] * Q[m][0] + D[a][gg][1] * Q[m][1] + D[a][gg][2] * Q[m][2]);
-      }
-      E[a][b] += twoKq0 * e2;
+      // the chiral part: sum over g != b of eps(m, b, g) d_a Q_g. . Q_m. (m = 3 - b - g);
+      // eps(m, b, g) = +1 for g = b + 1, m = b + 2 and -1 for g = b + 2, m = b + 1 (mod 3)
+      const int g1 = (b + 1) % 3, g2 = (b + 2) % 3;
+      const T e2 = (D[a][g1][0] * Q[g2][0] + D[a][g1][1] * Q[g2][1] + D[a][g1][2] * Q[g2][2]) -
+                   (D[a][g2][0] * Q[g1][0] + D[a][g2][1] * Q[g1][1] + D[a][g2][2] * Q[g1][2]);
+      E[a][b] = E[a][b] + twoKq0 * e2;
     }
   T trq3 = T(0), qc = T(0);
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      trq3 += Q[a][b] * S2[a][b];
-      qc += Q[a][b] * C[a][b];
+      trq3 = trq3 + Q[a][b] * S2[a][b];
+      qc = qc + Q[a][b] * Cm[a][b];
     }
-  const T fp = T(0.5) * A0 * (T(1) - g / T(3)) * trq2 - A0g / T(3) * trq3 + T(0.25) * A0g * trq2 * trq2 +
-               T(0.5) * Kgrad2 + twoKq0 * qc + T(2) * K * q0 * q0 * trq2;
+  const C fb2 = C(0.5) * A0 * (C(1) - g * third), fb4 = C(0.25) * A0g;
+  const T fp = (fb2 * trq2 - A0g3 * trq3) + fb4 * (trq2 * trq2) + C(0.5) * Kgrad2 + twoKq0 * qc +
+               (C(2) * K * q0 * q0) * trq2;
   T Am[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) Am[a][b] = Q[a][0] * H[0][b] + Q[a][1] * H[1][b] + Q[a][2] * H[2][b];
   const T qh = Am[0][0] + Am[1][1] + Am[2][2];
-  const T xi = P.xi;
+  const C twoxi = C(2) * xi, twoxi3 = twoxi * third;
+  const T qh2 = twoxi * qh;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const T dlt = a == b ? T(1) : T(0);
-      p[3 * a + b] = fp * dlt + T(2) * xi * (Q[a][b] + dlt / T(3)) * qh - xi * (Am[a][b] + Am[b][a]) -
-                     T(2) * xi / T(3) * H[a][b] - E[a][b] + Am[a][b] - Am[b][a];
+      // 2 xi (Q + I/3) Q:H - xi (A + A^T) - (2 xi/3) H - E + A - A^T, plus f' on the diagonal
+      T v = qh2 * Q[a][b] - xi * (Am[a][b] + Am[b][a]) - twoxi3 * H[a][b] - E[a][b] + (Am[a][b] - Am[b][a]);
+      if (a == b) v = v + (fp + third * qh2);
+      p[3 * a + b] = v;
     }
   *fprime = fp;
 }

@@ -13,6 +13,7 @@
 #include <cstdio>
 
 #include "lclb_dev.cuh"
+#include "lclb_f2.cuh"
 #include "lclb_internal.h"
 
 namespace lclb {
@@ -634,8 +635,137 @@ __device__ __forceinline__ void stress_tile(const DevBox& B, const int4 td, int 
   if (mode & FORCE_ACC) warp_flush_colloid(B.col, my_c, my_acc, 6);
 }
 
+// ---------------------------------------------------------------------------
+// two-node paths of the FP32 kernels (boxes of even width)
+// ---------------------------------------------------------------------------
+// A lane holds the nodes x and x + 1 (x even) of its row, so a warp covers 64
+// columns: the fields move as float2, the x-neighbours of the pair come from
+// the adjacent lanes by one shuffle per component, and the per-node
+// arithmetic of the two nodes runs together in packed FP32x2 (f2).  A pair
+// with a node next to a solid or wall sends its fluid nodes through the
+// per-warp queue of the one-node path.
+__device__ __forceinline__ f2 ld2(const float* p) { return f2(__ldg(reinterpret_cast<const float2*>(p))); }
+__device__ __forceinline__ void st2(float* p, f2 v) { *reinterpret_cast<float2*>(p) = v.v; }
+
+template <bool CG>
+__device__ __forceinline__ f2 ldx2(const float* p) {
+  const float2* q = reinterpret_cast<const float2*>(p);
+  if constexpr (CG) return f2(__ldcg(q));
+  else return f2(__ldg(q));
+}
+
+// The pair's values of a field row shifted by -s (s = +1: the nodes x - 1, x;
+// s = -1: x + 1, x + 2), from the float2 v of the nodes x, x + 1 of the same
+// row.  All lanes call it; edge lanes load the outside node from src_row.
+template <bool CG>
+__device__ __forceinline__ f2 shift_pair(f2 v, int s, int lane, bool valid, int x, int nx, const float* src_row) {
+  const float left = __shfl_up_sync(0xffffffffu, v.v.y, 1);
+  const float right = __shfl_down_sync(0xffffffffu, v.v.x, 1);
+  if (s > 0) {
+    float l = left;
+    if (valid && lane == 0) l = ldx<CG>(src_row + (x == 0 ? nx - 1 : x - 1));
+    return f2(l, v.v.x);
+  }
+  float r = right;
+  if (valid && (lane == TX - 1 || x + 2 >= nx)) r = ldx<CG>(src_row + (x + 2 >= nx ? x + 2 - nx : x + 2));
+  return f2(v.v.y, r);
+}
+
+// Push node j (when cond) onto the warp's queue sq[wy], evaluating 32 queued
+// nodes with fn(j) whenever the queue holds 32 or more.  All lanes call it.
+template <typename Fn>
+__device__ __forceinline__ void queue_push(int (*sq)[2 * TX], int wy, int lane, int& nq, bool cond, int j, Fn fn) {
+  const unsigned nb = __ballot_sync(0xffffffffu, cond);
+  if (!nb) return;
+  if (cond) sq[wy][nq + __popc(nb & ((1u << lane) - 1u))] = j;
+  nq += __popc(nb);
+  __syncwarp();
+  if (nq >= TX) {
+    fn(sq[wy][lane]);
+    __syncwarp();
+    nq -= TX;
+    if (lane < nq) sq[wy][lane] = sq[wy][TX + lane];
+    __syncwarp();
+  }
+}
+
+// Stored-stress kernel, two nodes per lane: H and P of the pair from packed
+// derivatives (the z-neighbours rolled down the column as in stress_tile).
+template <int TY>
+__device__ __forceinline__ void stress_tile_pair(const DevBox& B, const int4 td, int zc, int mode,
+                                                 int (*sq)[2 * TX]) {
+  if (!B.p.lc_on) return;
+  const int lane = threadIdx.x, wy = threadIdx.y;
+  const float* __restrict__ Q = static_cast<const float*>(B.Q[B.st->qpar]);
+  float* __restrict__ Hb = static_cast<float*>(B.H);
+  float* __restrict__ Pb = static_cast<float*>(B.P);
+  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  const size_t N = (size_t)B.N;
+  const int x = td.y + 2 * lane, y = td.z + wy;
+  const int zend = min(td.w + zc, nz);
+  const bool valid = x < nx && y < ny;
+  const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+  int my_c = -1;
+  double my_acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int nq = 0;
+  auto near_fn = [&](int j) {
+    stress_node<float, true>(B, B.pf, Q, Hb, Pb, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j], mode, my_c,
+                             my_acc);
+  };
+  f2 qz[2][5];  // the pair's Q at z - 1 and z, rolled down the z march
+  {
+    const int zm = td.w > 0 ? td.w - 1 : (B.wall_z ? -1 : nz - 1);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      qz[0][k] = (valid && zm >= 0) ? ld2(Q + k * N + x + nx * (y + ny * zm)) : f2(0.f);
+      qz[1][k] = valid ? ld2(Q + k * N + x + nx * (y + ny * td.w)) : f2(0.f);
+    }
+  }
+  for (int z = td.w; z < zend; ++z) {
+    const int row = nx * (y + ny * z);
+    const int i = x + row;
+    const unsigned m2 = valid ? (unsigned)*reinterpret_cast<const uint16_t*>(B.mask + i) : 0x0101u;
+    const uint8_t mA = (uint8_t)(m2 & 0xffu), mB = (uint8_t)(m2 >> 8);
+    const bool fA = (mA & IDMASK) == 0, fB = (mB & IDMASK) == 0;
+    const bool plain = fA && fB && !(mA & NEAR) && !(mB & NEAR);
+    const int zp = z + 1 < nz ? z + 1 : (B.wall_z ? -1 : 0);
+    f2 qn[6][5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      qn[4][k] = (valid && zp >= 0) ? ld2(Q + k * N + x + nx * (y + ny * zp)) : f2(0.f);
+      qn[5][k] = qz[0][k];
+      qn[0][k] = shift_pair<false>(qz[1][k], -1, lane, valid, x, nx, Q + k * N + row);
+      qn[1][k] = shift_pair<false>(qz[1][k], 1, lane, valid, x, nx, Q + k * N + row);
+    }
+    if (plain) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        qn[2][k] = ld2(Q + k * N + x + nx * (yp + ny * z));
+        qn[3][k] = ld2(Q + k * N + x + nx * (ym + ny * z));
+      }
+      f2 dq[3][5], lap[5], h[5], p[9], fp;
+      derivatives(qz[1], qn, dq, lap);
+      lc_node_d<f2, true, float>(B.pf, qz[1], dq, lap, h, p, &fp);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) st2(Hb + c * N + i, h[c]);
+#pragma unroll
+      for (int c = 0; c < 9; ++c) st2(Pb + c * N + i, p[c]);
+    }
+    queue_push(sq, wy, lane, nq, fA && !plain, i, near_fn);
+    queue_push(sq, wy, lane, nq, fB && !plain, i + 1, near_fn);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      qz[0][k] = qz[1][k];
+      qz[1][k] = qn[4][k];
+    }
+  }
+  if (lane < nq) near_fn(sq[wy][lane]);
+  __syncwarp();
+  if (mode & FORCE_ACC) warp_flush_colloid(B.col, my_c, my_acc, 6);
+}
+
 template <typename T, int TY>
-__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 : 256) / (TX * TY)) k_stress(
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 384 : 256) / (TX * TY)) k_stress(
     const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
     double* __restrict__ part) {
   __shared__ DevBox B;
@@ -644,6 +774,12 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 : 256) / (TX * 
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
     load_box(B, boxes, td.x, cur_box);
+    if constexpr (sizeof(T) == 4) {
+      if (pair_box(B)) {
+        stress_tile_pair<TY>(B, td, zc, mode, sq);
+        continue;
+      }
+    }
     stress_tile<T, TY>(B, td, zc, mode, sq);
   }
 }
@@ -1107,8 +1243,214 @@ __device__ __forceinline__ void lc_tile(const DevBox& B, const int4 td, int zc, 
   }
 }
 
+// Q update, two nodes per lane (FP32 boxes of even width; tiles 64 wide): the
+// Beris-Edwards update of lc_update_node for the nodes x, x + 1 at once, in
+// packed FP32x2 arithmetic, with Q, u, H and the BF16 remainder of Q moved as
+// pairs.  The upwind choice of each face flux is taken per node.
+__device__ __forceinline__ f2 sel2(bool ca, bool cb, f2 a, f2 b) {
+  return f2(ca ? a.v.x : b.v.x, cb ? a.v.y : b.v.y);
+}
+
+__device__ __forceinline__ void lc_update_pair(const DevBox& B, float* __restrict__ Qo,
+                                               __nv_bfloat16* __restrict__ Lout, int i, const f2 qi[5],
+                                               const f2 qn[6][5], const f2 ui[3], const f2 un[6][3], const f2 h_[5],
+                                               const f2 lo[5], float& rsum, float& rmax) {
+  const PhysT<float>& PP = B.pf;
+  const size_t N = (size_t)B.N;
+  const float Gam = PP.Gamma, xi = PP.xi;
+  f2 h[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) h[k] = h_[k];
+  // velocity gradient W_ab = d_b u_a
+  f2 W[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) W[a][b] = f2(0.5f * (un[2 * b][a] - un[2 * b + 1][a]));
+  // upwind advective fluxes through the six faces (no solid faces here)
+  f2 adv[5] = {f2(0.f), f2(0.f), f2(0.f), f2(0.f), f2(0.f)};
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const int ax = d >> 1;
+    const f2 uf = f2(0.5f * (ui[ax] + un[d][ax]));
+    const bool plus = (d & 1) == 0;
+    const bool pa = uf.v.x > 0.f, pb = uf.v.y > 0.f;
+    const bool ta = plus ? pa : !pa, tb = plus ? pb : !pb;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const f2 up = sel2(ta, tb, qi[k], qn[d][k]);
+      adv[k] = plus ? adv[k] + uf * up : adv[k] - uf * up;
+    }
+  }
+  // co-rotation S = xi (D Qt + Qt D) + (Om Q - Q Om) - 2 xi Qt Tr(Q W), Qt = Q + I/3
+  f2 D[3][3], Om[3][3], Qm[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      D[a][b] = f2(0.5f * (W[a][b] + W[b][a]));
+      Om[a][b] = f2(0.5f * (W[a][b] - W[b][a]));
+      Qm[a][b] = qab(qi, a, b);
+    }
+  f2 trQW = f2(0.f);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) trQW = trQW + Qm[a][b] * D[a][b];
+  const int ia[5] = {0, 0, 0, 1, 1}, ib[5] = {0, 1, 2, 1, 2};
+  const float twoxi = 2.f * xi, xi23 = 2.f * xi / 3.f, third = 1.f / 3.f;
+  f2 dQ[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      f2 sacc = f2(0.f);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const f2 dq = D[a][c] * Qm[c][b] + Qm[a][c] * D[c][b];
+        sacc = sacc + xi * dq;
+        sacc = sacc + Om[a][c] * Qm[c][b];
+        sacc = sacc - Qm[a][c] * Om[c][b];
+      }
+      sacc = sacc + xi23 * D[a][b];
+      const f2 qt = a == b ? Qm[a][b] + third : Qm[a][b];
+      sacc = sacc - twoxi * (qt * trQW);
+      dQ[a][b] = sacc;
+    }
+  const f2 tr = dQ[0][0] + dQ[1][1] + dQ[2][2];
+  {
+    // local part of H(hi + lo) - H(hi) to first order (as lc_update_node)
+    const float A0 = PP.A0, g = PP.gamma, K = PP.K, q0 = PP.q0;
+    f2 Lm[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Lm[a][b] = qab(lo, a, b);
+    f2 trq2 = f2(0.f), trql = f2(0.f);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        trq2 = trq2 + Qm[a][b] * Qm[a][b];
+        trql = trql + Qm[a][b] * Lm[a][b];
+      }
+    const float A0g = A0 * g;
+    const f2 cb = (-A0 * (1.f - g / 3.f) - 4.f * K * q0 * q0 - 6.f * K) - A0g * trq2;
+    const f2 trql2 = f2(2.f * A0g * trql);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int a = ia[k], b = ib[k];
+      f2 ql = f2(0.f);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ql = ql + Qm[a][c] * Lm[c][b] + Lm[a][c] * Qm[c][b];
+      if (a == b) ql = ql - (2.f / 3.f) * trql;
+      h[k] = h[k] + cb * lo[k] + A0g * ql - trql2 * qi[k];
+    }
+  }
+  f2 d5[5];
+  const f2 tr3 = f2(third * tr);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    f2 v = Gam * h[k] + dQ[ia[k]][ib[k]] - adv[k];
+    if (ia[k] == ib[k]) v = v - tr3;
+    d5[k] = v;
+    // compensated storage: hi + lo + v carried exactly into (hi, lo) (two-sum)
+    const f2 sv = lo[k] + v;
+    const f2 hn = qi[k] + sv;
+    const f2 bb = hn - qi[k];
+    const f2 err = (qi[k] - (hn - bb)) + (sv - bb);
+    st2(Qo + (size_t)k * N + i, hn);
+    *reinterpret_cast<__nv_bfloat162*>(Lout + (size_t)k * N + i) = __float22bfloat162_rn(err.v);
+  }
+  const f2 dzz = -(d5[0] + d5[3]);
+  const f2 r2 = d5[0] * d5[0] + d5[3] * d5[3] + dzz * dzz + 2.f * (d5[1] * d5[1] + d5[2] * d5[2] + d5[4] * d5[4]);
+  rsum += r2.v.x + r2.v.y;
+  float mx = fmaxf(fabsf(dzz.v.x), fabsf(dzz.v.y));
+#pragma unroll
+  for (int k = 0; k < 5; ++k) mx = fmaxf(mx, fmaxf(fabsf(d5[k].v.x), fabsf(d5[k].v.y)));
+  rmax = fmaxf(rmax, mx);
+}
+
+template <int TY, bool CG>
+__device__ __forceinline__ void lc_tile_pair(const DevBox& B, const int4 td, int zc, double* part, double* sred,
+                                             int (*sq)[2 * TX]) {
+  if (!B.p.lc_on) return;
+  const int tid = threadIdx.x + TX * threadIdx.y;
+  const int lane = threadIdx.x, wy = threadIdx.y;
+  const int qpar = B.st->qpar;
+  const float* __restrict__ Q = static_cast<const float*>(B.Q[qpar]);
+  float* __restrict__ Qo = static_cast<float*>(B.Q[qpar ^ 1]);
+  const __nv_bfloat16* __restrict__ Lin = B.Qlo[qpar];
+  __nv_bfloat16* __restrict__ Lout = B.Qlo[qpar ^ 1];
+  const float* __restrict__ U = static_cast<const float*>(B.u);
+  const float* __restrict__ Hb = static_cast<const float*>(B.H);
+  const int nx = B.nx, ny = B.ny, nz = B.nz;
+  const size_t N = (size_t)B.N;
+  const int x = td.y + 2 * lane, y = td.z + wy;
+  const int zend = min(td.w + zc, nz);
+  const bool valid = x < nx && y < ny;
+  const int yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+  float rsum = 0.f, rmax = 0.f;
+  int nq = 0;
+  auto near_fn = [&](int j) {
+    lc_update_node<float, true, CG>(B, B.pf, Q, Qo, Lin, Lout, U, j % nx, (j / nx) % ny, j / (nx * ny), j, B.mask[j],
+                                    rsum, rmax);
+  };
+  for (int z = td.w; z < zend; ++z) {
+    const int row = nx * (y + ny * z);
+    const int i = x + row;
+    const unsigned m2 = valid ? (unsigned)*reinterpret_cast<const uint16_t*>(B.mask + i) : 0x0101u;
+    const uint8_t mA = (uint8_t)(m2 & 0xffu), mB = (uint8_t)(m2 >> 8);
+    const bool fA = (mA & IDMASK) == 0, fB = (mB & IDMASK) == 0;
+    const bool plain = fA && fB && !(mA & NEAR) && !(mB & NEAR);
+    f2 qi[5], ui[3], qn[6][5], un[6][3];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      qi[k] = valid ? ldx2<false>(Q + k * N + i) : f2(0.f);
+      qn[0][k] = shift_pair<false>(qi[k], -1, lane, valid, x, nx, Q + k * N + row);
+      qn[1][k] = shift_pair<false>(qi[k], 1, lane, valid, x, nx, Q + k * N + row);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      ui[a] = valid ? ldx2<CG>(U + a * N + i) : f2(0.f);
+      un[0][a] = shift_pair<CG>(ui[a], -1, lane, valid, x, nx, U + a * N + row);
+      un[1][a] = shift_pair<CG>(ui[a], 1, lane, valid, x, nx, U + a * N + row);
+    }
+    if (plain) {
+      const int zp = z + 1 == nz ? 0 : z + 1, zm = z == 0 ? nz - 1 : z - 1;  // no wall next to a plain node
+      const int jr[4] = {x + nx * (yp + ny * z), x + nx * (ym + ny * z), x + nx * (y + ny * zp),
+                         x + nx * (y + ny * zm)};
+      f2 h[5], lo[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) qn[2 + d][k] = ldx2<false>(Q + k * N + jr[d]);
+        h[k] = ldx2<CG>(Hb + k * N + i);
+        lo[k] = f2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(Lin + k * N + i)));
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) un[2 + d][a] = ldx2<CG>(U + a * N + jr[d]);
+      lc_update_pair(B, Qo, Lout, i, qi, qn, ui, un, h, lo, rsum, rmax);
+    }
+    queue_push(sq, wy, lane, nq, valid && fA && !plain, i, near_fn);
+    queue_push(sq, wy, lane, nq, valid && fB && !plain, i + 1, near_fn);
+  }
+  if (lane < nq) near_fn(sq[wy][lane]);
+  __syncwarp();
+  if (part) {
+    double rs[2] = {(double)rsum, (double)rmax};
+    block_sum<2>(rs, sred, true);
+    if (tid == 0) {
+      part[0] = rs[0];
+      part[1] = rs[1];
+    }
+  }
+}
+
 template <typename T, int TY>
-__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 640 : 256) / (TX * TY)) k_lc(
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 384 : 256) / (TX * TY)) k_lc(
     const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
     double* __restrict__ part) {
   __shared__ DevBox B;
@@ -1118,6 +1460,12 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 640 : 256) / (TX * 
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
     load_box(B, boxes, td.x, cur_box);
+    if constexpr (sizeof(T) == 4) {
+      if (pair_box(B)) {
+        lc_tile_pair<TY, false>(B, td, zc, (mode & LC_RESID) ? part + 2 * t : nullptr, sred, sq);
+        continue;
+      }
+    }
     lc_tile<T, TY, false>(B, td, zc, (mode & LC_RESID) ? part + 2 * t : nullptr, sred, sq);
   }
 }
@@ -1374,9 +1722,25 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 : 256) / (TX * 
       load_box(B, boxes, I.box, cur_box);
       const int4 td = make_int4(I.box, I.x0, I.y0, I.z0);
       switch (I.kind) {
-        case ITEM_STRESS: stress_tile<T, TY>(B, td, zc, FORCE_ACC, sq); break;
+        case ITEM_STRESS:
+          if constexpr (sizeof(T) == 4) {
+            if (pair_box(B)) {
+              stress_tile_pair<TY>(B, td, zc, FORCE_ACC, sq);
+              break;
+            }
+          }
+          stress_tile<T, TY>(B, td, zc, FORCE_ACC, sq);
+          break;
         case ITEM_LB: lbp_tile<T, TY, true>(B, td, zc, sq); break;
-        case ITEM_LC: lc_tile<T, TY, true>(B, td, zc, part + 2 * (size_t)I.part, sred, sq); break;
+        case ITEM_LC:
+          if constexpr (sizeof(T) == 4) {
+            if (pair_box(B)) {
+              lc_tile_pair<TY, true>(B, td, zc, part + 2 * (size_t)I.part, sred, sq);
+              break;
+            }
+          }
+          lc_tile<T, TY, true>(B, td, zc, part + 2 * (size_t)I.part, sred, sq);
+          break;
         case ITEM_LINKS: links_chunk<T, true>(B, I.x0, LINK_CHUNK, sblk, &s_sc0); break;
         default: colloid_box<true>(B, commit != 0); break;
       }
