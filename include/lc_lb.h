@@ -205,22 +205,24 @@ int lc_lb_diagnostics(lc_lb* h, lc_diag* out);
 
 /* Allocation-free diagnostics: the paper has no counterpart; this exists for
  * callers that cannot allocate device memory at the point of the call --
- * code that runs while another stream of the device is being captured into
- * a CUDA graph in global or relaxed mode (where cudaMalloc is not permitted),
  * allocator or out-of-memory handlers that must not re-enter an allocator,
- * and loops that cannot afford the device-wide synchronisation of
- * cudaMalloc/cudaFree.  It fills mass, momentum, n_fluid, n_defect and step
- * of *out exactly as lc_lb_diagnostics does (the other fields are set to 0)
- * and calls no cudaMalloc, cudaFree or allocating library routine.  Its
- * scratch is a static device array of 384 KiB + 64 B that every GPU loading
- * this library holds until the process exits; it serves boxes of at most
- * 2,097,152 nodes (a 128^3 box) and returns LC_ERR_ARG for larger ones.  The
- * first call on a device looks up the array's device address (once per
- * device, with that device current), so make that first call before any
- * stream capture.  All calls on a device share the array, which keeps the
- * last call's contents (each call overwrites every record it reads), so two
- * calls whose GPU work overlaps -- e.g. two handles on different streams --
- * race.  Synchronises the handle's stream. */
+ * code that runs under a fixed device-memory budget, and loops that cannot
+ * afford the device-wide synchronisation of cudaMalloc/cudaFree.  It fills
+ * mass, momentum, n_fluid, n_defect and step of *out exactly as
+ * lc_lb_diagnostics does (the other fields are set to 0) and calls no
+ * cudaMalloc, cudaFree or allocating library routine.  Its scratch is a
+ * static device array of 384 KiB + 64 B that every GPU loading this library
+ * holds until the process exits; it serves boxes of at most 2,097,152 nodes
+ * (a 128^3 box) and returns LC_ERR_ARG for larger ones.  The first call on a
+ * device looks up the array's device address (once per device, with that
+ * device current) and keeps it for the process: the call assumes the
+ * device's primary context (the runtime's default) and must not be used
+ * after cudaDeviceReset on that device.  The device current at the call must
+ * be the one the handle was created on (LC_ERR_ARG otherwise).  All calls on
+ * a device share the array, which keeps the last call's contents (each call
+ * overwrites every record it reads), so two calls whose GPU work overlaps --
+ * e.g. two handles on different streams -- race.  Synchronises the handle's
+ * stream. */
 int lc_lb_diagnostics_noalloc(lc_lb* h, lc_diag* out);
 
 /* Profiling: run nsteps steps without the graph and with every kernel on

@@ -1,9 +1,9 @@
 """lc_lb_diagnostics_noalloc: the allocation-free diagnostics give what lc_lb_diagnostics gives.
 
 Some callers cannot allocate device memory at the point of the call (for
-example code that runs while another stream is being captured into a CUDA
-graph, where cudaMalloc is not permitted, or an out-of-memory handler); this
-entry point keeps its scratch in a static device array instead.  The test
+example an out-of-memory handler that must not re-enter an allocator, or code
+under a fixed device-memory budget); this entry point keeps its scratch in a
+static device array instead.  The test
 calls both entry points through the C ABI twice in a row (with steps in
 between) and also checks that a box above the stated size limit is refused.
 It sits in a file of its own that pytest collects last.
