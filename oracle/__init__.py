@@ -65,6 +65,8 @@ def lib():
             L.oracle_set_colloid_velocity.argtypes = [vp, C.c_int, dp, dp]
             L.oracle_get_colloid.argtypes = [vp, C.c_int, dp]
             L.oracle_step.argtypes = [vp, C.c_int]
+            L.oracle_contact.restype = C.c_int
+            L.oracle_contact.argtypes = [vp, C.POINTER(C.c_long)]
             L.oracle_links.restype = C.c_long
             L.oracle_links.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int8), C.POINTER(C.c_int16),
                                        C.c_long]
@@ -189,6 +191,16 @@ class Oracle:
 
     def step(self, n=1):
         self.L.oracle_step(self.h, int(n))
+
+    def contact(self):
+        """First contact since the last call, as ``(step, colloid, partner)``
+        (partner -1: a z wall), or None.  A mobile colloid whose move would
+        touch a wall or another colloid keeps its position (the oracle's
+        reading; the paper treats no contact)."""
+        a = (C.c_long * 3)()
+        if self.L.oracle_contact(self.h, a) == 0:
+            return None
+        return int(a[0]), int(a[1]), int(a[2])
 
     @property
     def step_count(self) -> int:

@@ -21,7 +21,9 @@
  *     advective fluxes at control-volume faces (Sec. 2.2, Fig. 1).
  *   - Q update: explicit Euler of Eq. 2 with the Beris-Edwards co-rotation term.
  *   - Colloid: the "molecular dynamics-like step" of Sec. 2.2 taken implicit
- *     in the velocity-dependent part of the link force (colloid_update).
+ *     in the velocity-dependent part of the link force (colloid_update); a
+ *     move into contact with another colloid or a wall is not made and is
+ *     reported (contact_resolve; the paper treats no contact).
  *
  * Parity status: every function below is pinned by a CPU test, including the
  * surface value at colloid faces (homeotropic normal at the solid node,
@@ -110,6 +112,8 @@ typedef struct {
   double resid_rms, resid_max;
   int nthreads;
   int last_error;
+  long contact_step; /* first contact since the caller last read it (-1: none), see contact_resolve */
+  int contact_c, contact_d;
 } oracle;
 
 /* ------------------------------------------------------------------ */
@@ -863,8 +867,65 @@ static void solve3(const double A_in[3][3], const double b_in[3], double x[3]) {
  * Omega' = Omega + (I + zw)^{-1} (T_hyd + T_LC), zw = sum 6 w rho0 (r x c)(r x c);
  * X += V'.  M = rho0 (4/3) pi a0^3 (neutrally buoyant), I = (2/5) M a0^2.
  * With no links (flow off) this is the explicit update. */
+/* Squared minimum-image distance of two colloid centres, summed left to right. */
+static double centre_dist2(const oracle* o, const ocolloid* A, const ocolloid* B) {
+  double d[3];
+  node_disp(o, A->X[0], A->X[1], A->X[2], B->X, d);
+  return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+}
+
+/* Contact partner of colloid c at the current positions: -1 for a z wall,
+ * the lowest index of a colloid it touches, or -2 for none.  The paper treats
+ * no contact (Sec. 3.2 leaves interactions between colloids to later work), so
+ * this is a reading: two colloids touch when their centres are closer than
+ * the sum of their radii, and a colloid touches a wall when its surface passes
+ * the plane of the half-way bounce-back, z = -1/2 or z = nz - 1/2 (the test
+ * that oracle_add_colloid applies). */
+static int contact_partner(const oracle* o, int c) {
+  const ocolloid* C = &o->col[c];
+  if (o->wall_z && (C->X[2] - C->a0 < -0.5 || C->X[2] + C->a0 > o->nz - 0.5)) return -1;
+  for (int d = 0; d < o->ncol; ++d) {
+    if (d == c) continue;
+    double s = C->a0 + o->col[d].a0;
+    if (centre_dist2(o, C, &o->col[d]) < s * s) return d;
+  }
+  return -2;
+}
+
+/* A mobile colloid whose new position touches a wall or another colloid keeps
+ * its position of the step before (its new velocities stand), so that no node
+ * lies inside two colloids and no colloid crosses a wall.  All mobile
+ * colloids are tested at the same positions, then those in contact are put
+ * back; as a colloid put back can be touched by another's move, this repeats
+ * until none is put back.  The first contact since the caller last read it
+ * (lowest colloid index of that pass, its partner from contact_partner, the
+ * step) is kept for the caller, who is told of it as an error. */
+static void contact_resolve(oracle* o, double Xold[][3]) {
+  int back[OMAXC] = {0};
+  for (int pass = 0; pass <= o->ncol; ++pass) {
+    int hit[OMAXC], any = 0;
+    for (int c = 0; c < o->ncol; ++c)
+      hit[c] = (o->col[c].mobile && !back[c]) ? contact_partner(o, c) : -2;
+    for (int c = 0; c < o->ncol; ++c) {
+      if (hit[c] == -2) continue;
+      if (o->contact_step < 0) {
+        o->contact_step = o->step;
+        o->contact_c = c;
+        o->contact_d = hit[c];
+      }
+      for (int a = 0; a < 3; ++a) o->col[c].X[a] = Xold[c][a];
+      back[c] = 1;
+      any = 1;
+    }
+    if (!any) break;
+  }
+}
+
 static void colloid_update(oracle* o) {
   int moved = 0;
+  double Xold[OMAXC][3];
+  for (int c = 0; c < o->ncol; ++c)
+    for (int a = 0; a < 3; ++a) Xold[c][a] = o->col[c].X[a];
   for (int c = 0; c < o->ncol; ++c) {
     ocolloid* C = &o->col[c];
     for (int a = 0; a < 3; ++a) {
@@ -897,6 +958,7 @@ static void colloid_update(oracle* o) {
     }
     moved = 1;
   }
+  if (moved) contact_resolve(o, Xold);
   if (moved) rediscretise(o);
 }
 
@@ -945,6 +1007,7 @@ oracle* oracle_create(int nx, int ny, int nz, int wall_z, const double* params, 
   o->g[0] = params[9]; o->g[1] = params[10]; o->g[2] = params[11];
   o->lc_on = lc_on; o->flow_on = flow_on;
   o->nthreads = 1;
+  o->contact_step = -1;
   long N = o->N;
   o->solid = (int16_t*)malloc(sizeof(int16_t) * (size_t)N);
   for (long i = 0; i < N; ++i) o->solid[i] = -1;
@@ -970,6 +1033,17 @@ void oracle_destroy(oracle* o) {
 }
 
 void oracle_set_threads(oracle* o, int n) { o->nthreads = n < 1 ? 1 : n; }
+
+/* First contact since the last call (see contact_resolve): returns 1 and
+ * out = (step, colloid, partner; -1 for a wall), then forgets it; 0 if none. */
+int oracle_contact(oracle* o, long* out) {
+  if (o->contact_step < 0) return 0;
+  out[0] = o->contact_step;
+  out[1] = o->contact_c;
+  out[2] = o->contact_d;
+  o->contact_step = -1;
+  return 1;
+}
 double oracle_S0(const oracle* o) { return o->S0; }
 long oracle_step_count(const oracle* o) { return o->step; }
 
@@ -1094,7 +1168,8 @@ void oracle_lc_fields(oracle* o, double* H5, double* P9, double* F3, double* fe)
 
 
 /* Adds a colloid of nominal radius a0 at X (Sec. 2.2).  Returns its index,
- * -1 on a bad argument, -2 if it overlaps another colloid or a wall. */
+ * -1 on a bad argument, -2 if it touches another colloid or a wall (the
+ * contact test of contact_partner) or shares a node with another colloid. */
 int oracle_add_colloid(oracle* o, const double* X, double a0, int anchoring, double w, int mobile,
                        const double* Fext) {
   if (o->ncol >= OMAXC || !(a0 > 0.0)) return -1;
@@ -1109,6 +1184,10 @@ int oracle_add_colloid(oracle* o, const double* X, double a0, int anchoring, dou
   C->M = o->rho0 * 4.0 / 3.0 * M_PI * a0 * a0 * a0;
   C->I = 0.4 * C->M * a0 * a0;
   int id = o->ncol;
+  for (int d = 0; d < o->ncol; ++d) {
+    double s = a0 + o->col[d].a0;
+    if (centre_dist2(o, C, &o->col[d]) < s * s) return -2;
+  }
   for (int z = 0; z < o->nz; ++z)
     for (int y = 0; y < o->ny; ++y)
       for (int x = 0; x < o->nx; ++x) {
