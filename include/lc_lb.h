@@ -38,7 +38,7 @@ enum {
   LC_ERR_ARG = -1,       /* bad argument (size, pointer, value range) */
   LC_ERR_CUDA = -2,      /* a CUDA runtime call failed */
   LC_ERR_OOM = -3,       /* the allocator returned NULL */
-  LC_ERR_OVERLAP = -4,   /* colloid overlaps another colloid or a wall */
+  LC_ERR_OVERLAP = -4,   /* colloid touches another colloid or a wall (add_colloid, or a move refused in a step) */
   LC_ERR_NONFINITE = -5, /* a reduction met NaN/Inf */
   LC_ERR_TIMEOUT = -6,   /* a bounded device-side wait gave up */
   LC_ERR_STATE = -7      /* call not valid in the handle's state */
@@ -136,7 +136,10 @@ int lc_lb_set_fields(lc_lb* h, int which, const void* src, size_t bytes, int src
  * anchoring LC_NORMAL (homeotropic) or LC_PLANAR; w = anchoring strength
  * (INFINITY or <= 0: the paper's fixed surface Q0); mobile = 1 lets the
  * colloid move under F_hyd + F_LC + F_ext.  Errors: LC_ERR_ARG (a0 <= 0,
- * more than 126 colloids), LC_ERR_OVERLAP.  *id_out receives its index. */
+ * more than 126 colloids), LC_ERR_OVERLAP (its centre is closer to another
+ * colloid's current centre than the sum of the radii, minimum image, or its
+ * surface passes a wall plane z = -1/2 or nz - 1/2).  *id_out receives its
+ * index. */
 int lc_lb_add_colloid(lc_lb* h, const double X[3], double a0, int anchoring, double w, int mobile,
                       const double F_ext[3], int* id_out);
 int lc_lb_set_colloid_velocity(lc_lb* h, int id, const double V[3], const double W[3]);
@@ -145,7 +148,15 @@ int lc_lb_set_colloid_force(lc_lb* h, int id, const double F_ext[3]);
 /* Advance nsteps coupled steps (Sec. 2.2 step order): LC stress and body
  * force, density/velocity, Q update (Eq. 2), collide + bounce-back + stream,
  * colloid update.  Asynchronous on the handle's stream; replays a captured
- * CUDA graph per step after the first call. */
+ * CUDA graph per step after the first call.
+ * Contact (the paper treats none): a mobile colloid whose move would bring
+ * it closer to another colloid than the sum of the radii, or its surface
+ * past a wall plane, is not moved in that step (its velocities are updated);
+ * the first such contact is reported as LC_ERR_OVERLAP, with the step, box
+ * and colloids in lc_lb_last_error, by the next call that synchronises
+ * (lc_lb_synchronize, lc_lb_relax, lc_lb_get_fields, lc_lb_get_colloid,
+ * lc_lb_get_forces, lc_lb_diagnostics), which clears it.  The state stays
+ * valid: no node is ever inside two colloids. */
 int lc_lb_step(lc_lb* h, int nsteps);
 
 /* Relax: steps in chunks of check_every until the residual (RMS of the Q

@@ -11,7 +11,8 @@ import math
 
 from ._binding import (  # noqa: F401
     LC_FP32, LC_FP64, LC_NORMAL, LC_PLANAR, LC_Q, LC_U, LC_RHO, LC_F_PRE, LC_FORCE, LcLbError, Solver, Batch, lib,
-    library_path,
+    library_path, LC_OK, LC_ERR_ARG, LC_ERR_CUDA, LC_ERR_OOM, LC_ERR_OVERLAP, LC_ERR_NONFINITE, LC_ERR_TIMEOUT,
+    LC_ERR_STATE,
 )
 
 

@@ -299,6 +299,7 @@ int write_state(Group* g, lc_lb* h, int pre_valid) {
   st.fpar = 0;
   st.qpar = 0;
   st.pre_valid = pre_valid;
+  st.cstep = -1;
   CK(cudaMemcpyAsync(h->hb.st, &st, sizeof(st), cudaMemcpyHostToDevice, g->stream), &h->err);
   return LC_OK;
 }
@@ -345,6 +346,7 @@ int make_box(Group* g, const lc_grid* G, const lc_params* p, lc_lb* h) {
   B.mask = (uint8_t*)galloc(g, N);
   B.col = (DevColloid*)galloc(g, sizeof(DevColloid) * MAXCOL);
   B.st = (DevState*)galloc(g, sizeof(DevState));
+  B.gerr = g->d_err;
   B.nlinks = (int*)galloc(g, sizeof(int));
   if (!B.f[0] || !B.f[1] || !B.Q[0] || !B.Q[1] || !B.u || !B.F || !B.H || !B.P || !B.mask || !B.col || !B.st ||
       !B.nlinks)
@@ -993,16 +995,43 @@ cudaError_t launch_dataflow(Group* g, int commit) {
                      g->ph[2].d_part, spin_limit(), commit, g->d_err, g->step_grid, g->stream);
 }
 
-// A wait of k_step that gave up leaves *d_err set: report it (and clear it).
+// The step kernels leave two error words in the group: d_err[0], a wait of
+// k_step that gave up (the state is invalid); d_err[1], a colloid move that
+// was not made because it would have touched another colloid or a wall (the
+// state is valid; the first contact is in the state of its box).  Reports the
+// first of them and clears both; synchronises the stream.
 int check_step_err(Group* g, std::string* err) {
-  if (g->variant != 3) return LC_OK;
   int* hv = reinterpret_cast<int*>(g->h_red + 63);
-  CK(cudaMemcpyAsync(hv, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream), err);
+  CK(cudaMemcpyAsync(hv, g->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, g->stream), err);
   CK(cudaStreamSynchronize(g->stream), err);
-  if (*hv == 0) return LC_OK;
-  CK(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream), err);
+  if (hv[0] == 0 && hv[1] == 0) return LC_OK;
+  const bool timeout = hv[0] != 0;
+  CK(cudaMemsetAsync(g->d_err, 0, 2 * sizeof(int), g->stream), err);
+  long long cstep = -1;
+  int cbox = -1, ccol = -1, cpartner = -2;
+  for (size_t b = 0; b < g->boxes.size(); ++b) {
+    DevState st{};
+    CK(cudaMemcpyAsync(&st, g->boxes[b]->hb.st, sizeof(st), cudaMemcpyDeviceToHost, g->stream), err);
+    CK(cudaStreamSynchronize(g->stream), err);
+    if (st.cstep < 0) continue;
+    if (cbox < 0) {
+      cbox = (int)b;
+      cstep = st.cstep;
+      ccol = st.ccol;
+      cpartner = st.cpartner;
+    }
+    st.cstep = -1;
+    st.err &= ~8;
+    CK(cudaMemcpyAsync(g->boxes[b]->hb.st, &st, sizeof(st), cudaMemcpyHostToDevice, g->stream), err);
+  }
   CK(cudaStreamSynchronize(g->stream), err);
-  return fail(err, LC_ERR_TIMEOUT, "a dependency wait of the persistent step kernel gave up; the state is invalid");
+  if (timeout) return fail(err, LC_ERR_TIMEOUT, "a dependency wait of the persistent step kernel gave up; the state is invalid");
+  if (cbox < 0) return fail(err, LC_ERR_STATE, "contact flagged with no box recording it");
+  char with[32];
+  if (cpartner == -1) snprintf(with, sizeof(with), "a wall");
+  else snprintf(with, sizeof(with), "colloid %d", cpartner);
+  return fail(err, LC_ERR_OVERLAP, "step %lld: colloid %d of box %d would touch %s; it was not moved", cstep, ccol,
+              cbox, with);
 }
 
 // One coupled step: fused stress + body force + collide/stream, then the Q
@@ -1391,6 +1420,27 @@ int lc_lb_add_colloid(lc_lb* h, const double X[3], double a0, int anchoring, dou
   if (h->grid.wall_z && (X[2] - a0 < -0.5 || X[2] + a0 > h->grid.nz - 0.5))
     return fail(&h->err, LC_ERR_OVERLAP, "colloid crosses a wall");
   Group* g = h->g;
+  if (!h->col.empty()) {
+    // contact test against the current positions (mobile colloids move on the device)
+    std::vector<DevColloid> cur(h->col.size());
+    CK(cudaMemcpyAsync(cur.data(), h->hb.col, sizeof(DevColloid) * cur.size(), cudaMemcpyDeviceToHost, g->stream),
+       &h->err);
+    CK(cudaStreamSynchronize(g->stream), &h->err);
+    const int L[3] = {h->grid.nx, h->grid.ny, h->grid.nz};
+    for (size_t d = 0; d < cur.size(); ++d) {
+      double r2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        double r = X[a] - cur[d].X[a];
+        if (a < 2 || !h->grid.wall_z) {
+          if (r >= 0.5 * L[a]) r -= L[a];
+          else if (r < -0.5 * L[a]) r += L[a];
+        }
+        r2 += r * r;
+      }
+      const double s = a0 + cur[d].a0;
+      if (r2 < s * s) return fail(&h->err, LC_ERR_OVERLAP, "colloid touches colloid %d", (int)d);
+    }
+  }
   DevColloid C;
   memset(&C, 0, sizeof(C));
   for (int a = 0; a < 3; ++a) {
@@ -1409,6 +1459,7 @@ int lc_lb_add_colloid(lc_lb* h, const double X[3], double a0, int anchoring, dou
   CK(cudaMemcpyAsync(h->hb.col + id, &C, sizeof(C), cudaMemcpyHostToDevice, g->stream), &h->err);
   h->col.push_back(C);
   h->hb.ncol = (int)h->col.size();
+  h->hb.nmobile += C.mobile;
   int rc = rebuild_geometry(h);
   if (rc) return rc;
   DevState st{};
@@ -1417,6 +1468,7 @@ int lc_lb_add_colloid(lc_lb* h, const double X[3], double a0, int anchoring, dou
   if (st.err & 4) {
     h->col.pop_back();
     h->hb.ncol = (int)h->col.size();
+    h->hb.nmobile -= C.mobile;
     st.err &= ~4;
     CK(cudaMemcpyAsync(h->hb.st, &st, sizeof(st), cudaMemcpyHostToDevice, g->stream), &h->err);
     rc = rebuild_geometry(h);
@@ -1682,6 +1734,7 @@ int lc_lb_diagnostics(lc_lb* h, lc_diag* out) {
   double sums[4];
   int rc = count_fluid(g, h, &nf, &nd, sums);
   if (rc) return rc;
+  if ((rc = check_step_err(g, &h->err))) return rc;
   out->n_fluid = nf;
   out->n_defect = nd;
   out->mass = (double)nf * h->hb.p.rho0 + sums[0];

@@ -70,15 +70,20 @@ struct DevState {
   int fpar;       // f[fpar] holds the current populations
   int qpar;       // Q[qpar] holds the current order parameter
   int pre_valid;  // f[fpar] holds pre-collision values: next collide reads them in place
-  int err;        // sticky error bits (1: link list overflow, 2: change list overflow, 4: overlap)
+  int err;        // sticky error bits (1: link list overflow, 2: change list overflow, 4: overlap, 8: contact)
   int nchg;       // nodes whose solid/fluid status changes after the colloid update of this step
   int pad;
   long long step;
+  // first contact since the host last read it (see resolve_contacts): the
+  // step, the colloid and its partner (-1: a z wall); cstep < 0: none
+  long long cstep;
+  int ccol, cpartner;
 };
 
 struct DevBox {
   int nx, ny, nz, wall_z;
-  int pair, pad0;       // 1: FP32 box of even width (two-node paths of the stress kernel and the Q update)
+  int pair;             // 1: FP32 box of even width (two-node paths of the stress kernel and the Q update)
+  int nmobile;          // mobile colloids in the box (the colloid update tests contacts when > 0)
   int N, ncol;
   int nlinks_cap, chg_cap;
   int* chg;             // change list: (node, colloid << 1 | uncovered) pairs
@@ -95,6 +100,7 @@ struct DevBox {
   uint8_t* mask;
   DevColloid* col;
   DevState* st;
+  int* gerr;            // error words of the box's group: [0] wait gave up, [1] contact in some box
   int* nlinks;          // device count of boundary links
   int* link_node;       // boundary links of this box, sorted by (colloid, node, dir)
   int8_t* link_dir;

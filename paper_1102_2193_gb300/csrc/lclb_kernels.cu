@@ -1594,6 +1594,72 @@ __device__ void solve_sym3(const double* a, double s, const double* b, double* x
 // velocity-dependent part of the link force is taken at the new velocity:
 // V' = V + (M + zv)^{-1} (F_hyd + F_lc + F_ext), W' = W + (I + zw)^{-1} (T_hyd + T_lc).
 // ---------------------------------------------------------------------------
+// Contact partner of colloid c at the current positions: -1 for a z wall,
+// the lowest index of a colloid it touches, -2 for none.  The paper treats no
+// contact (interactions between colloids are left to later work, Sec. 3.2);
+// the reading taken: two colloids touch when their centres (minimum image)
+// are closer than the sum of their radii, a colloid touches a wall when its
+// surface passes the plane of the half-way bounce-back, z = -1/2 or nz - 1/2.
+__device__ int contact_partner(const DevBox& B, int c) {
+  const DevColloid& C = B.col[c];
+  if (B.wall_z && (C.X[2] - C.a0 < -0.5 || C.X[2] + C.a0 > B.nz - 0.5)) return -1;
+  for (int d = 0; d < B.ncol; ++d) {
+    if (d == c) continue;
+    double r[3];
+    disp(B, C.X[0], C.X[1], C.X[2], B.col[d].X, r);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(r[0], r[0]), __dmul_rn(r[1], r[1])), __dmul_rn(r[2], r[2]));
+    const double s = __dadd_rn(C.a0, B.col[d].a0);
+    if (r2 < __dmul_rn(s, s)) return d;
+  }
+  return -2;
+}
+
+// A mobile colloid whose new position touches a wall or another colloid is
+// put back where it was before this step's move (its new velocities stand),
+// so that no node is ever inside two colloids.  Every mobile colloid is tested
+// at the same positions, then those in contact are put back; a colloid put
+// back can be touched by another's move, so the test repeats until a pass
+// puts none back.  The first contact since the host last read it (lowest
+// colloid index of that pass) is kept in the box state and flagged in the
+// group's error words; the host reports it as LC_ERR_OVERLAP.  All threads of
+// the block call this (it holds block barriers).
+__device__ void resolve_contacts(DevBox& B, int tid, int nthr) {
+  __shared__ signed char s_hit[MAXCOL];  // -2 no contact, else the partner
+  __shared__ unsigned char s_back[MAXCOL];
+  __shared__ int s_any;
+  for (int c = tid; c < B.ncol; c += nthr) s_back[c] = 0;
+  for (int pass = 0; pass <= B.ncol; ++pass) {
+    __syncthreads();
+    for (int c = tid; c < B.ncol; c += nthr)
+      s_hit[c] = (signed char)((B.col[c].mobile && !s_back[c]) ? contact_partner(B, c) : -2);
+    if (tid == 0) s_any = 0;
+    __syncthreads();
+    for (int c = tid; c < B.ncol; c += nthr) {
+      if (s_hit[c] == -2) continue;
+      DevColloid& C = B.col[c];
+      for (int a = 0; a < 3; ++a) C.X[a] = C.Xb[a];
+      s_back[c] = 1;
+      s_any = 1;
+    }
+    if (tid == 0) {
+      DevState* st = B.st;
+      for (int c = 0; c < B.ncol; ++c) {
+        if (s_hit[c] == -2) continue;
+        if (st->cstep < 0) {
+          st->cstep = st->step;
+          st->ccol = c;
+          st->cpartner = s_hit[c];
+        }
+        st->err |= 8;
+        atomicOr(B.gerr + 1, 1);
+        break;
+      }
+    }
+    __syncthreads();
+    if (!s_any) break;
+  }
+}
+
 template <bool CG>
 __device__ __forceinline__ void colloid_box(DevBox& B, bool commit = true) {
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
@@ -1642,6 +1708,7 @@ __device__ __forceinline__ void colloid_box(DevBox& B, bool commit = true) {
     }
     for (int k = 0; k < 24; ++k) C.acc[k] = 0.0;
   }
+  if (B.nmobile) resolve_contacts(B, tid, nthr);
   if (tid == 0) {
     DevState* st = B.st;
     if (B.p.flow_on) {
@@ -2138,7 +2205,10 @@ __device__ __forceinline__ int region_size(const DevBox& B, const DevColloid& C)
   return min(B.nx, e) * min(B.ny, e) * min(B.nz, e);
 }
 
-// New solid owner of node (x,y,z): colloid index + 1, or 0.
+// New solid owner of node (x,y,z): colloid index + 1, or 0.  No node is
+// inside two colloids: add_colloid refuses a colloid that touches another and
+// the colloid update puts back a move into contact (resolve_contacts), so the
+// first colloid found is the only one.
 __device__ __forceinline__ int new_owner(const DevBox& B, int x, int y, int z) {
   for (int c = 0; c < B.ncol; ++c)
     if (inside_colloid(B, x, y, z, B.col[c])) return c + 1;

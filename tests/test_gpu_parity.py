@@ -250,6 +250,62 @@ def test_two_mobile_colloids_approaching(P, prec):
     assert (ng == no).all() and (dg == do).all() and (cg == co).all()
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_contact_between_colloids_refused_and_reported(P, prec):
+    """Two mobile colloids pushed together by external forces until their
+    centres come closer than the sum of the radii: that move is not made, on
+    the GPU as in the oracle (the oracle's contact reading, pinned by hand in
+    test_oracle_contact), the next synchronising call reports the first
+    contact as LC_ERR_OVERLAP with its step and colloids, and the state after
+    it (colloids held, fluid and Q still stepping) matches the oracle."""
+    L = (28, 22, 20)
+    prm = dict(synth.NEMATIC, q0=2 * math.pi / 20)
+    cols = [dict(X=(9.3, 10.6, 9.2), a0=3.5, anchoring=0, w=float("inf"), mobile=True, F_ext=(1.2, 0.0, 0.0)),
+            dict(X=(16.8, 10.9, 9.9), a0=3.0, anchoring=1, w=0.02, mobile=True, F_ext=(-1.2, 0.0, 0.0))]
+    g, o = make_pair(P, L, prm, P.LC_FP32 if prec == "f32" else P.LC_FP64, colloids=cols,
+                     init=("helix", 2, 1e-2, 5))
+    g.step(60)
+    o.step(60)
+    oc = o.contact()
+    assert oc is not None and oc[1:] == (0, 1), oc
+    with pytest.raises(P.LcLbError) as e:
+        g.synchronize()
+    assert e.value.code == P.LC_ERR_OVERLAP
+    assert f"step {oc[0]}: colloid 0 of box 0 would touch colloid 1;" in str(e.value), str(e.value)
+    g.synchronize()  # reported once
+    compare(g, o, TOL32 if prec == "f32" else TOL64, ncol=2, radii=[3.5, 3.0])
+    d = np.asarray(g.colloid(1)["X"]) - np.asarray(g.colloid(0)["X"])
+    assert np.linalg.norm(d) >= 6.5
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_wall_contact_refused_and_reported(P, prec):
+    """A mobile colloid pushed into a no-slip wall stops where its surface
+    would pass the bounce-back plane z = -1/2; GPU against oracle."""
+    cols = [dict(X=(7.7, 8.2, 3.15), a0=3.5, anchoring=1, w=0.01, mobile=True, F_ext=(0.0, 0.0, -1.0))]
+    g, o = make_pair(P, (16, 16, 24), dict(synth.NEMATIC), P.LC_FP32 if prec == "f32" else P.LC_FP64,
+                     wall_z=True, colloids=cols, init=("uniaxial", (0, 0, 1), 1e-3, 2))
+    g.step(30)
+    o.step(30)
+    oc = o.contact()
+    assert oc is not None and oc[1:] == (0, -1), oc
+    with pytest.raises(P.LcLbError) as e:
+        g.colloid(0)
+    assert e.value.code == P.LC_ERR_OVERLAP
+    assert f"step {oc[0]}: colloid 0 of box 0 would touch a wall;" in str(e.value), str(e.value)
+    compare(g, o, TOL32 if prec == "f32" else TOL64, ncol=1, radii=[3.5])
+    assert g.colloid(0)["X"][2] - 3.5 >= -0.5
+
+
+def test_add_rejects_touching_colloid_with_no_shared_node(P):
+    g = P.Solver(16, 12, 12)
+    g.add_colloid((5.5, 5.5, 5.5), 0.6)  # holds no node
+    with pytest.raises(P.LcLbError) as e:
+        g.add_colloid((6.6, 5.5, 5.5), 0.6)  # centres 1.1 < 1.2 apart
+    assert e.value.code == P.LC_ERR_OVERLAP
+    g.add_colloid((6.75, 5.5, 5.5), 0.6)
+
+
 def test_lc_off_and_flow_off_switches(P):
     L = (20, 16, 12)
     for lc, flow in ((False, True), (True, False)):
