@@ -691,6 +691,9 @@ __device__ __forceinline__ void queue_push(int (*sq)[2 * TX], int wy, int lane, 
 
 // Stored-stress kernel, two nodes per lane: H and P of the pair from packed
 // derivatives (the z-neighbours rolled down the column as in stress_tile).
+// The loads of the next plane (mask, the column's z + 1 and the rows y +- 1)
+// are issued before the current plane is evaluated, so their latency is
+// covered by that plane's arithmetic rather than by other warps.
 template <int TY>
 __device__ __forceinline__ void stress_tile_pair(const DevBox& B, const int4 td, int zc, int mode,
                                                  int (*sq)[2 * TX]) {
@@ -713,6 +716,18 @@ __device__ __forceinline__ void stress_tile_pair(const DevBox& B, const int4 td,
                              my_acc);
   };
   f2 qz[2][5];  // the pair's Q at z - 1 and z, rolled down the z march
+  f2 pz[5], pyp[5], pym[5];  // next plane's loads: the pair's Q at z + 1, the rows y + 1 and y - 1 at z
+  unsigned pm2;              // and the pair's mask bytes at z
+  auto fetch = [&](int z) {
+    const int zp = z + 1 < nz ? z + 1 : (B.wall_z ? -1 : 0);
+    pm2 = valid ? (unsigned)*reinterpret_cast<const uint16_t*>(B.mask + x + nx * (y + ny * z)) : 0x0101u;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      pz[k] = (valid && zp >= 0) ? ld2(Q + k * N + x + nx * (y + ny * zp)) : f2(0.f);
+      pyp[k] = valid ? ld2(Q + k * N + x + nx * (yp + ny * z)) : f2(0.f);
+      pym[k] = valid ? ld2(Q + k * N + x + nx * (ym + ny * z)) : f2(0.f);
+    }
+  };
   {
     const int zm = td.w > 0 ? td.w - 1 : (B.wall_z ? -1 : nz - 1);
 #pragma unroll
@@ -721,28 +736,29 @@ __device__ __forceinline__ void stress_tile_pair(const DevBox& B, const int4 td,
       qz[1][k] = valid ? ld2(Q + k * N + x + nx * (y + ny * td.w)) : f2(0.f);
     }
   }
+  if (td.w < zend) fetch(td.w);
   for (int z = td.w; z < zend; ++z) {
     const int row = nx * (y + ny * z);
     const int i = x + row;
-    const unsigned m2 = valid ? (unsigned)*reinterpret_cast<const uint16_t*>(B.mask + i) : 0x0101u;
+    const unsigned m2 = pm2;
     const uint8_t mA = (uint8_t)(m2 & 0xffu), mB = (uint8_t)(m2 >> 8);
     const bool fA = (mA & IDMASK) == 0, fB = (mB & IDMASK) == 0;
     const bool plain = fA && fB && !(mA & NEAR) && !(mB & NEAR);
-    const int zp = z + 1 < nz ? z + 1 : (B.wall_z ? -1 : 0);
     f2 qn[6][5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      qn[4][k] = (valid && zp >= 0) ? ld2(Q + k * N + x + nx * (y + ny * zp)) : f2(0.f);
+      qn[4][k] = pz[k];
+      qn[2][k] = pyp[k];
+      qn[3][k] = pym[k];
       qn[5][k] = qz[0][k];
+    }
+    if (z + 1 < zend) fetch(z + 1);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
       qn[0][k] = shift_pair<false>(qz[1][k], -1, lane, valid, x, nx, Q + k * N + row);
       qn[1][k] = shift_pair<false>(qz[1][k], 1, lane, valid, x, nx, Q + k * N + row);
     }
     if (plain) {
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        qn[2][k] = ld2(Q + k * N + x + nx * (yp + ny * z));
-        qn[3][k] = ld2(Q + k * N + x + nx * (ym + ny * z));
-      }
       f2 dq[3][5], lap[5], h[5], p[9], fp;
       derivatives(qz[1], qn, dq, lap);
       lc_node_d<f2, true, float>(B.pf, qz[1], dq, lap, h, p, &fp);
@@ -1450,7 +1466,7 @@ __device__ __forceinline__ void lc_tile_pair(const DevBox& B, const int4 td, int
 }
 
 template <typename T, int TY>
-__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 384 : 256) / (TX * TY)) k_lc(
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 : 256) / (TX * TY)) k_lc(
     const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
     double* __restrict__ part) {
   __shared__ DevBox B;
