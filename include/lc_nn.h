@@ -55,6 +55,16 @@ int lc_nn_up2_concat_bwd(const float* dout, float* dlo, float* dskip, int S, int
  * (FP64; caller zeroes it), grad (npos x cout, may be NULL) = dL/dout. */
 int lc_nn_mse(const float* out, const float* base, const float* target, const float* fluid, float* grad,
               double* loss, int npos, int cout, double inv_count, void* stream);
+/* Long-wavelength term of the loss: the masked error d = (base + out[:, 0:5]
+ * - target) * [fluid[p] > 0] averaged over cubes of b^3 positions (box S^3,
+ * position p = x + S (y + S z), S divisible by b), E = mean of d over a cube:
+ * *loss += inv_count * sum over cubes and components of E^2 (FP64; caller
+ * zeroes it or adds to the MSE's), grad[p][c] += inv_count * 2 E / b^3 at
+ * fluid positions, c < 5 (accumulated into the MSE's gradient; may be NULL).
+ * blk: caller-owned device scratch of (S/b)^3 * 5 floats.  With b = 1 it is
+ * the MSE itself.  Errors: LC_NN_ERR_ARG (b < 1, S % b != 0, cout < 5). */
+int lc_nn_mse_coarse(const float* out, const float* base, const float* target, const float* fluid, float* grad,
+                     double* loss, float* blk, int S, int b, int cout, double inv_count, void* stream);
 /* Adam step (step >= 1) on FP32 masters p with moments m, v; p16 (BF16 copy) may be NULL. */
 int lc_nn_adam(float* p, const float* g, float* m, float* v, void* p16, size_t n, float lr, float b1, float b2,
                float eps, int step, void* stream);

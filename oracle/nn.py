@@ -97,6 +97,27 @@ def loss(y, base, target, fluid):
     return L, dy
 
 
+def loss_coarse(y, base, target, fluid, b):
+    """Long-wavelength term: the masked error averaged over cubes of b^3
+    positions, E = mean over the cube of (base + y[..., :5] - target) [fluid],
+    L = sum over cubes and components of E^2 / n with n the MSE's count
+    (5 x fluid positions); dL/dy[p] = 2 E(cube of p) / (b^3 n) at fluid
+    positions.  Written with explicit loops over the cubes."""
+    D, H, W = fluid.shape
+    d = (y[..., :5] + base - target) * fluid[..., None]
+    n = fluid.sum() * 5.0
+    L = 0.0
+    dy = np.zeros_like(y)
+    for z0 in range(0, D, b):
+        for y0 in range(0, H, b):
+            for x0 in range(0, W, b):
+                E = d[z0:z0 + b, y0:y0 + b, x0:x0 + b].sum(axis=(0, 1, 2)) / float(b ** 3)
+                L += float((E * E).sum())
+                dy[z0:z0 + b, y0:y0 + b, x0:x0 + b, :5] = (2.0 * E / (b ** 3 * n)) * fluid[z0:z0 + b, y0:y0 + b,
+                                                                                          x0:x0 + b, None]
+    return L / n, dy
+
+
 def backward(params, a, dy):
     g = {}
     relu = lambda d, act: d * (act > 0)  # noqa: E731

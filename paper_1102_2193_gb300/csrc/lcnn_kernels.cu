@@ -286,6 +286,52 @@ __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ b
   if (threadIdx.x == 0) atomicAdd(loss, s[0] * inv_count);
 }
 
+// Cube means of the masked error (one thread per cube and component) and
+// their squared sum; then each fluid position's share of the gradient.
+__global__ void k_mse_coarse_blocks(const float* __restrict__ out, const float* __restrict__ base,
+                                    const float* __restrict__ target, const float* __restrict__ fluid,
+                                    float* __restrict__ blk, double* __restrict__ loss, int S, int b, int cout,
+                                    double inv_count) {
+  __shared__ double s[256];
+  const int nc = S / b;
+  const int ncube = nc * nc * nc;
+  double acc = 0.0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ncube * 5; t += gridDim.x * blockDim.x) {
+    const int cube = t / 5, c = t % 5;
+    const int cx = cube % nc, cy = (cube / nc) % nc, cz = cube / (nc * nc);
+    double sum = 0.0;
+    for (int dz = 0; dz < b; ++dz)
+      for (int dy = 0; dy < b; ++dy)
+        for (int dx = 0; dx < b; ++dx) {
+          const size_t p = (size_t)(cx * b + dx) + (size_t)S * ((cy * b + dy) + (size_t)S * (cz * b + dz));
+          if (fluid[p] > 0.f) sum += (double)(out[p * cout + c] + base[p * 5 + c] - target[p * 5 + c]);
+        }
+    const double e = sum / ((double)b * b * b);
+    blk[t] = (float)e;
+    acc += e * e;
+  }
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int d = blockDim.x / 2; d > 0; d >>= 1) {
+    if (threadIdx.x < d) s[threadIdx.x] += s[threadIdx.x + d];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(loss, s[0] * inv_count);
+}
+
+__global__ void k_mse_coarse_grad(const float* __restrict__ fluid, const float* __restrict__ blk,
+                                  float* __restrict__ grad, int S, int b, int cout, double inv_count) {
+  const int nc = S / b;
+  const size_t npos = (size_t)S * S * S;
+  const float g = (float)(2.0 * inv_count / ((double)b * b * b));
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < npos; p += (size_t)gridDim.x * blockDim.x) {
+    if (!(fluid[p] > 0.f)) continue;
+    const int x = (int)(p % S), y = (int)((p / S) % S), z = (int)(p / ((size_t)S * S));
+    const int cube = x / b + nc * (y / b + nc * (z / b));
+    for (int c = 0; c < 5; ++c) grad[p * cout + c] += g * blk[cube * 5 + c];
+  }
+}
+
 // Adam on FP32 masters with a BF16 working copy.
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
                        __nv_bfloat16* __restrict__ p16, size_t n, float lr, float b1, float b2, float eps, float c1,
@@ -474,6 +520,17 @@ int lc_nn_up2_concat_bwd(const float* dout, float* dlo, float* dskip, int S, int
 int lc_nn_mse(const float* out, const float* base, const float* target, const float* fluid, float* grad,
               double* loss, int npos, int cout, double inv_count, void* stream) {
   k_mse<<<grid_for(npos), 256, 0, (cudaStream_t)stream>>>(out, base, target, fluid, grad, loss, npos, cout, inv_count);
+  return cudaGetLastError() == cudaSuccess ? LC_NN_OK : LC_NN_ERR_CUDA;
+}
+
+int lc_nn_mse_coarse(const float* out, const float* base, const float* target, const float* fluid, float* grad,
+                     double* loss, float* blk, int S, int b, int cout, double inv_count, void* stream) {
+  if (b < 1 || S < 1 || S % b != 0 || cout < 5 || !blk || !loss) return LC_NN_ERR_ARG;
+  const int nc = S / b;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_mse_coarse_blocks<<<grid_for((size_t)nc * nc * nc * 5), 256, 0, st>>>(out, base, target, fluid, blk, loss, S, b,
+                                                                           cout, inv_count);
+  if (grad) k_mse_coarse_grad<<<grid_for((size_t)S * S * S), 256, 0, st>>>(fluid, blk, grad, S, b, cout, inv_count);
   return cudaGetLastError() == cudaSuccess ? LC_NN_OK : LC_NN_ERR_CUDA;
 }
 

@@ -135,13 +135,22 @@ class UNet:
         self._conv("c4", a["u0"])
         self._conv("head", a["c4"])
 
-    def loss_and_grad(self, target_q=None, grad=True) -> float:
-        """Masked MSE of Q_init + y[:, :5] against the target (set with set_target)."""
+    def loss_and_grad(self, target_q=None, grad=True, coarse=None) -> float:
+        """Masked MSE of Q_init + y[:, :5] against the target (set with set_target).
+        ``coarse = (b, weight)`` adds weight x the same error averaged over cubes
+        of b^3 nodes (lc_nn_mse_coarse), which weights the long-wavelength part
+        of the error by up to b^3 relative to node-scale noise."""
         nf = self.nf
         self.loss.zero_()
+        inv = 1.0 / max(nf * 5.0, 1.0)
         _ok(self.L.lc_nn_mse(_p(self.y), _p(self.base), _p(self.target), _p(self.fluid),
-                             _p(self.dy) if grad else None, _p(self.loss), self.S**3, 16, 1.0 / max(nf * 5.0, 1.0),
-                             self.sp), "mse")
+                             _p(self.dy) if grad else None, _p(self.loss), self.S**3, 16, inv, self.sp), "mse")
+        if coarse is not None:
+            b, wgt = coarse
+            blk = self.torch.empty(((self.S // b)**3 * 5,), dtype=self.torch.float32, device=self.dev)
+            _ok(self.L.lc_nn_mse_coarse(_p(self.y), _p(self.base), _p(self.target), _p(self.fluid),
+                                        _p(self.dy) if grad else None, _p(self.loss), _p(blk), self.S, int(b), 16,
+                                        inv * float(wgt), self.sp), "mse_coarse")
         return float(self.loss.item())
 
     def set_target(self, q_soa):

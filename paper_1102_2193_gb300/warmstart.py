@@ -57,8 +57,10 @@ def _setup(box, spec, S):
     box.add_colloid((c, c, c), spec["R"], LC_NORMAL, spec["w"])
 
 
-def relaxed_dataset(specs, S, steps, torch, precision=LC_FP32, chunk=32):
-    """Inputs and relaxed targets, all as FP64 device tensors."""
+def relaxed_dataset(specs, S, steps, torch, precision=LC_FP32, chunk=32, tol=None, log=None):
+    """Inputs and relaxed targets, all as FP64 device tensors.  Each batch of
+    boxes is stepped ``steps`` times or, with ``tol``, relaxed until every box's
+    RMS residual is <= tol (at most ``steps`` steps)."""
     data = []
     for k in range(0, len(specs), chunk):
         part = specs[k:k + chunk]
@@ -66,7 +68,12 @@ def relaxed_dataset(specs, S, steps, torch, precision=LC_FP32, chunk=32):
         for box, sp in zip(B.boxes, part):
             _setup(box, sp, S)
         inputs = [solver_fields(box, torch) for box in B.boxes]
-        B.step(steps)
+        if tol is None:
+            B.step(steps)
+        else:
+            n, r = B.relax(tol=tol, max_steps=steps, check_every=2000)
+            if log:
+                log(f"batch {k // chunk}: {n} steps, residuals {float(np.min(r)):.2e}..{float(np.max(r)):.2e}")
         for box, sp, (solid, q0) in zip(B.boxes, part, inputs):
             q = torch.empty((5, S**3), dtype=torch.float64, device="cuda")
             box.get_fields(LC_Q, q)
@@ -75,7 +82,9 @@ def relaxed_dataset(specs, S, steps, torch, precision=LC_FP32, chunk=32):
     return data
 
 
-def train(net: UNet, data, epochs: int, lr: float = 2e-3, seed: int = 0, log=None):
+def train(net: UNet, data, epochs: int, lr: float = 2e-3, seed: int = 0, log=None, coarse=None):
+    """Adam over the boxes in a seeded order; ``coarse = (b, weight)`` adds the
+    long-wavelength term of ``UNet.loss_and_grad``."""
     rng = np.random.default_rng(seed)
     hist = []
     for ep in range(epochs):
@@ -85,7 +94,7 @@ def train(net: UNet, data, epochs: int, lr: float = 2e-3, seed: int = 0, log=Non
             net.set_input(d["solid"], d["q0"], d["spec"]["R"], d["spec"]["pitch"], d["spec"]["w"])
             net.set_target(d["target"])
             net.forward()
-            tot += net.loss_and_grad()
+            tot += net.loss_and_grad(coarse=coarse)
             net.backward()
             net.adam(lr=lr * (0.5 ** (ep / max(1, epochs // 3))))
         hist.append(tot / len(data))
@@ -258,7 +267,10 @@ def main(argv=None):
     ap.add_argument("--S", type=int, default=64)
     ap.add_argument("--train", type=int, default=48)
     ap.add_argument("--hold", type=int, default=8)
-    ap.add_argument("--relax-steps", type=int, default=30000)
+    ap.add_argument("--relax-steps", type=int, default=30000,
+                    help="steps of each training box (with --target-tol: the step limit)")
+    ap.add_argument("--target-tol", type=float, default=None,
+                    help="relax the training boxes to this RMS residual instead of a fixed step count")
     ap.add_argument("--epochs", type=int, default=15)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--tol32", type=float, default=1e-8)
@@ -274,6 +286,8 @@ def main(argv=None):
     ap.add_argument("--only-batch", action="store_true", help="run the batched comparison only")
     ap.add_argument("--any-pitch", action="store_true", help="also pitches whose Q period does not divide S (the "
                     "periodic box then frustrates the helix, which relaxes by slowly changing its pitch)")
+    ap.add_argument("--coarse-b", type=int, default=0, help="cube size of the long-wavelength loss term (0: off)")
+    ap.add_argument("--coarse-weight", type=float, default=64.0, help="weight of the long-wavelength loss term")
     ap.add_argument("--seed", type=int, default=1000)
     a = ap.parse_args(argv)
     if a.only_batch:
@@ -284,12 +298,13 @@ def main(argv=None):
         return res
     t0 = time.perf_counter()
     specs = (geometries if a.any_pitch else commensurate_geometries)(a.train + a.hold, a.S, a.seed)
-    data = relaxed_dataset(specs, a.S, a.relax_steps, torch)
+    data = relaxed_dataset(specs, a.S, a.relax_steps, torch, tol=a.target_tol, log=lambda m: print(m, flush=True))
     t_data = time.perf_counter() - t0
     print(f"dataset: {len(data)} relaxed boxes in {t_data:.1f} s", flush=True)
     net = UNet(S=a.S, seed=a.seed)
     t1 = time.perf_counter()
-    hist = train(net, data[:a.train], a.epochs, a.lr, log=lambda m: print(m, flush=True))
+    hist = train(net, data[:a.train], a.epochs, a.lr, log=lambda m: print(m, flush=True),
+                 coarse=(a.coarse_b, a.coarse_weight) if a.coarse_b else None)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
     res = dict(n_params=net.n_params(), data_s=t_data, train_s=t_train, train_loss=hist,

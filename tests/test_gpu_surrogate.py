@@ -163,6 +163,34 @@ def test_training_reduces_the_loss(P):
     assert losses[-1] < 0.6 * losses[0], losses[::25]
 
 
+def test_coarse_loss_matches_reference(P):
+    """lc_nn_mse_coarse (cube means of the masked error, accumulated onto the
+    MSE's loss and gradient) against the FP64 reference, on a ragged fluid
+    mask and b = 1, 2, 4."""
+    L = P.lib()
+    S, cout = 16, 16
+    rng = np.random.default_rng(11)
+    y = rng.standard_normal((S, S, S, cout)).astype(np.float32).astype(np.float64)
+    base = rng.standard_normal((S, S, S, 5)).astype(np.float32).astype(np.float64)
+    target = rng.standard_normal((S, S, S, 5)).astype(np.float32).astype(np.float64)
+    fluid = (rng.uniform(size=(S, S, S)) > 0.3).astype(np.float64)
+    n = fluid.sum() * 5.0
+    for b in (1, 2, 4):
+        Lr0, g0 = nn.loss(y, base, target, fluid)
+        Lr1, g1 = nn.loss_coarse(y, base, target, fluid, b)
+        dy, db, dt, df = (dev32(a.reshape(S**3, -1)) for a in (y, base, target, fluid))
+        grad = torch.empty((S**3, cout), dtype=torch.float32, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        blk = torch.empty(((S // b)**3 * 5,), dtype=torch.float32, device="cuda")
+        assert L.lc_nn_mse(ptr(dy), ptr(db), ptr(dt), ptr(df), ptr(grad), ptr(loss), S**3, cout, 1.0 / n, None) == 0
+        assert L.lc_nn_mse_coarse(ptr(dy), ptr(db), ptr(dt), ptr(df), ptr(grad), ptr(loss), ptr(blk), S, b, cout,
+                                  1.0 / n, None) == 0
+        torch.cuda.synchronize()
+        assert abs(loss.item() - (Lr0 + Lr1)) <= 1e-6 * (Lr0 + Lr1), (b, loss.item(), Lr0 + Lr1)
+        assert rel(grad.cpu().numpy().reshape(S, S, S, cout), g0 + g1) < 1e-5, b
+    assert L.lc_nn_mse_coarse(ptr(dy), ptr(db), ptr(dt), ptr(df), None, ptr(loss), ptr(blk), S, 3, cout, 1.0, None) != 0
+
+
 def test_trilinear_upsampling_of_smooth_field(P):
     L = P.lib()
     S = 16

@@ -88,3 +88,41 @@ def test_unet_backward_by_finite_differences():
             fd = (Lp - Lm) / (2 * e)
             an = g[f"{name}_{k}"][j]
             assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, k, fd, an)
+
+
+def test_coarse_loss_pins():
+    """The long-wavelength loss term: b = 1 is the masked MSE itself; an error
+    field constant on each cube keeps its whole weight, one alternating in
+    sign inside every cube has none; the gradient matches central finite
+    differences of the loss."""
+    rng = np.random.default_rng(5)
+    S = 8
+    y = rng.standard_normal((S, S, S, 16))
+    base = rng.standard_normal((S, S, S, 5))
+    target = rng.standard_normal((S, S, S, 5))
+    fluid = (rng.uniform(size=(S, S, S)) > 0.25).astype(float)
+    L1, g1 = nn.loss_coarse(y, base, target, fluid, 1)
+    L0, g0 = nn.loss(y, base, target, fluid)
+    assert abs(L1 - L0) <= 1e-13 * L0 and np.abs(g1 - g0).max() <= 1e-15
+    # all fluid, error constant on each 4^3 cube: the cube means are the error itself
+    ones = np.ones((S, S, S))
+    e = np.repeat(np.repeat(np.repeat(rng.standard_normal((2, 2, 2, 5)), 4, 0), 4, 1), 4, 2)
+    yc = np.zeros((S, S, S, 16))
+    yc[..., :5] = e
+    Lc, _ = nn.loss_coarse(yc, np.zeros((S, S, S, 5)), np.zeros((S, S, S, 5)), ones, 4)
+    assert abs(Lc - (e[::4, ::4, ::4] ** 2).sum() / (S ** 3 * 5.0)) <= 1e-14
+    # checkerboard error: every cube mean vanishes
+    zz, yy, xx = np.meshgrid(np.arange(S), np.arange(S), np.arange(S), indexing="ij")
+    yc[..., :5] = ((-1.0) ** (xx + yy + zz))[..., None] * np.arange(1, 6)
+    assert nn.loss_coarse(yc, np.zeros((S, S, S, 5)), np.zeros((S, S, S, 5)), ones, 2)[0] < 1e-28
+    L, g = nn.loss_coarse(y, base, target, fluid, 4)
+    h = 1e-6
+    for _ in range(12):
+        j = tuple(int(rng.integers(0, s)) for s in (S, S, S)) + (int(rng.integers(0, 5)),)
+        old = y[j]
+        y[j] = old + h
+        Lp = nn.loss_coarse(y, base, target, fluid, 4)[0]
+        y[j] = old - h
+        Lm = nn.loss_coarse(y, base, target, fluid, 4)[0]
+        y[j] = old
+        assert abs((Lp - Lm) / (2 * h) - g[j]) <= 1e-8 * max(1.0, abs(g[j]))
