@@ -172,6 +172,7 @@ def lib(use_torch_allocator: bool = True):
         L.lc_nn_up2_concat.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, vp]
         L.lc_nn_up2_concat_bwd.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, vp]
         L.lc_nn_mse.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int, C.c_int, C.c_double, vp]
+        L.lc_nn_mse_coarse.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_double, vp]
         L.lc_nn_adam.argtypes = [vp, vp, vp, vp, vp, C.c_size_t, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
                                  vp]
         L.lc_nn_pack_input.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double, vp, vp, vp, vp, C.c_int, C.c_int,
