@@ -63,6 +63,7 @@ def lib():
             L.oracle_add_colloid.restype = C.c_int
             L.oracle_add_colloid.argtypes = [vp, dp, C.c_double, C.c_int, C.c_double, C.c_int, dp]
             L.oracle_set_colloid_velocity.argtypes = [vp, C.c_int, dp, dp]
+            L.oracle_set_colloid_torque.argtypes = [vp, C.c_int, dp]
             L.oracle_get_colloid.argtypes = [vp, C.c_int, dp]
             L.oracle_step.argtypes = [vp, C.c_int]
             L.oracle_contact.restype = C.c_int
@@ -182,6 +183,9 @@ class Oracle:
 
     def set_colloid_velocity(self, cid, V, W=(0, 0, 0)):
         self.L.oracle_set_colloid_velocity(self.h, int(cid), _dp(_vec(V)), _dp(_vec(W)))
+
+    def set_colloid_torque(self, cid, T):
+        self.L.oracle_set_colloid_torque(self.h, int(cid), _dp(_vec(T)))
 
     def colloid(self, cid) -> dict:
         a = np.empty(27)

@@ -91,7 +91,7 @@ typedef struct {
   double a0, w; /* w <= 0 or inf: strong anchoring (the paper's fixed Q0) */
   int anchoring; /* 0 = normal (homeotropic), 1 = planar */
   int mobile;
-  double Fext[3];
+  double Fext[3], Text[3]; /* external force and torque */
   double M, I;
   double Fh[3], Th[3], Flc[3], Tlc[3]; /* forces and torques of the last step */
   double imp[3], aimp[3];              /* momentum / angular momentum received */
@@ -864,7 +864,7 @@ static void solve3(const double A_in[3][3], const double b_in[3], double x[3]) {
  * 6 w rho0 c c; taking the zv V part at the new velocity,
  *   (M + zv) V' = M V + (F_hyd + zv V) + F_LC + F_ext,
  * i.e. V' = V + (M + zv)^{-1} (F_hyd + F_LC + F_ext), and likewise
- * Omega' = Omega + (I + zw)^{-1} (T_hyd + T_LC), zw = sum 6 w rho0 (r x c)(r x c);
+ * Omega' = Omega + (I + zw)^{-1} (T_hyd + T_LC + T_ext), zw = sum 6 w rho0 (r x c)(r x c);
  * X += V'.  M = rho0 (4/3) pi a0^3 (neutrally buoyant), I = (2/5) M a0^2.
  * With no links (flow off) this is the explicit update. */
 /* Squared minimum-image distance of two colloid centres, summed left to right. */
@@ -940,7 +940,7 @@ static void colloid_update(oracle* o) {
         Aw[a][b] = C->zw[a][b] + (a == b ? C->I : 0.0);
       }
       bv[a] = C->Fh[a] + C->Flc[a] + C->Fext[a];
-      bw[a] = C->Th[a] + C->Tlc[a];
+      bw[a] = C->Th[a] + C->Tlc[a] + C->Text[a];
     }
     solve3(Av, bv, dv);
     solve3(Aw, bw, dw);
@@ -1202,6 +1202,12 @@ int oracle_add_colloid(oracle* o, const double* X, double a0, int anchoring, dou
         if (inside(o, x, y, z, C)) o->solid[i] = (int16_t)id;
       }
   return id;
+}
+
+/* External torque on colloid c (a rotating colloid; the paper's colloids
+ * take only the hydrodynamic and LC torques). */
+void oracle_set_colloid_torque(oracle* o, int c, const double* T) {
+  for (int a = 0; a < 3; ++a) o->col[c].Text[a] = T[a];
 }
 
 void oracle_set_colloid_velocity(oracle* o, int c, const double* V, const double* W) {
