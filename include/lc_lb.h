@@ -144,6 +144,11 @@ int lc_lb_add_colloid(lc_lb* h, const double X[3], double a0, int anchoring, dou
                       const double F_ext[3], int* id_out);
 int lc_lb_set_colloid_velocity(lc_lb* h, int id, const double V[3], const double W[3]);
 int lc_lb_set_colloid_force(lc_lb* h, int id, const double F_ext[3]);
+/* External torque T_ext on colloid id (a rotating colloid: the paper's
+ * colloids feel only the hydrodynamic and LC torques, Sec. 2.2); a mobile
+ * colloid's update then takes W' = W + (I + zw)^{-1} (T_hyd + T_LC + T_ext).
+ * Errors: LC_ERR_ARG (no colloid id, T_ext NULL).  Synchronises. */
+int lc_lb_set_colloid_torque(lc_lb* h, int id, const double T_ext[3]);
 
 /* Advance nsteps coupled steps (Sec. 2.2 step order): LC stress and body
  * force, density/velocity, Q update (Eq. 2), collide + bounce-back + stream,

@@ -127,6 +127,7 @@ def lib(use_torch_allocator: bool = True):
         L.lc_lb_add_colloid.argtypes = [vp, dp, C.c_double, C.c_int, C.c_double, C.c_int, dp, ip]
         L.lc_lb_set_colloid_velocity.argtypes = [vp, C.c_int, dp, dp]
         L.lc_lb_set_colloid_force.argtypes = [vp, C.c_int, dp]
+        L.lc_lb_set_colloid_torque.argtypes = [vp, C.c_int, dp]
         L.lc_lb_step.argtypes = [vp, C.c_int]
         L.lc_lb_relax.argtypes = [vp, C.c_double, C.c_longlong, C.c_int, C.POINTER(C.c_longlong), dp]
         L.lc_lb_get_fields.argtypes = [vp, C.c_int, vp, C.c_size_t, C.c_int]
@@ -314,6 +315,9 @@ class Solver:
 
     def set_colloid_force(self, cid, F_ext):
         self._check(self.L.lc_lb_set_colloid_force(self.h, int(cid), _dp(_v3(F_ext))))
+
+    def set_colloid_torque(self, cid, T_ext):
+        self._check(self.L.lc_lb_set_colloid_torque(self.h, int(cid), _dp(_v3(T_ext))))
 
     def colloid(self, cid) -> dict:
         a = np.empty(27)

@@ -1480,7 +1480,8 @@ int lc_lb_add_colloid(lc_lb* h, const double X[3], double a0, int anchoring, dou
   return LC_OK;
 }
 
-static int colloid_rmw(lc_lb* h, int id, const double* V, const double* W, const double* Fext) {
+static int colloid_rmw(lc_lb* h, int id, const double* V, const double* W, const double* Fext,
+                       const double* Text = nullptr) {
   if (int rc = h_check(h)) return rc;
   if (id < 0 || id >= (int)h->col.size()) return fail(&h->err, LC_ERR_ARG, "no colloid %d", id);
   Group* g = h->g;
@@ -1491,6 +1492,7 @@ static int colloid_rmw(lc_lb* h, int id, const double* V, const double* W, const
     if (V) C.V[a] = C.Vb[a] = V[a];
     if (W) C.W[a] = C.Wb[a] = W[a];
     if (Fext) C.Fext[a] = Fext[a];
+    if (Text) C.Text[a] = Text[a];
   }
   CK(cudaMemcpyAsync(h->hb.col + id, &C, sizeof(C), cudaMemcpyHostToDevice, g->stream), &h->err);
   CK(cudaStreamSynchronize(g->stream), &h->err);
@@ -1502,6 +1504,11 @@ int lc_lb_set_colloid_velocity(lc_lb* h, int id, const double V[3], const double
 }
 
 int lc_lb_set_colloid_force(lc_lb* h, int id, const double F_ext[3]) { return colloid_rmw(h, id, nullptr, nullptr, F_ext); }
+
+int lc_lb_set_colloid_torque(lc_lb* h, int id, const double T_ext[3]) {
+  if (!T_ext) return fail(h ? &h->err : nullptr, LC_ERR_ARG, "null torque");
+  return colloid_rmw(h, id, nullptr, nullptr, nullptr, T_ext);
+}
 
 int lc_lb_step(lc_lb* h, int nsteps) {
   if (int rc = h_check(h)) return rc;

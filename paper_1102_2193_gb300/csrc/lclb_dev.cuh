@@ -55,7 +55,7 @@ struct DevColloid {
   double X[3], V[3], W[3];
   double Xb[3], Vb[3], Wb[3];
   double a0, w, M, I;
-  double Fext[3];
+  double Fext[3], Text[3];  // external force and torque
   int anchoring, mobile, strong, pad;
   double wfac;     // weight of Q0 in the surface value: w / (K + w), 1 for strong anchoring
   double acc[24];  // step sums: F_hyd, T_hyd, F_lc, T_lc, then the link drag tensors zv, zw (6 each, xx xy xz yy yz zz)

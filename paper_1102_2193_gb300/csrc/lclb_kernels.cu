@@ -1608,7 +1608,7 @@ __device__ void solve_sym3(const double* a, double s, const double* b, double* x
 // k_colloid: colloid update ("molecular dynamics-like step", Sec. 2.2) and the
 // end-of-step parity flip.  One block per box, one thread per colloid.  The
 // velocity-dependent part of the link force is taken at the new velocity:
-// V' = V + (M + zv)^{-1} (F_hyd + F_lc + F_ext), W' = W + (I + zw)^{-1} (T_hyd + T_lc).
+// V' = V + (M + zv)^{-1} (F_hyd + F_lc + F_ext), W' = W + (I + zw)^{-1} (T_hyd + T_lc + T_ext).
 // ---------------------------------------------------------------------------
 // Contact partner of colloid c at the current positions: -1 for a z wall,
 // the lowest index of a colloid it touches, -2 for none.  The paper treats no
@@ -1705,7 +1705,8 @@ __device__ __forceinline__ void colloid_box(DevBox& B, bool commit = true) {
     if (C.mobile) {
       const double fv[3] = {C.Fh[0] + C.Flc[0] + C.Fext[0], C.Fh[1] + C.Flc[1] + C.Fext[1],
                             C.Fh[2] + C.Flc[2] + C.Fext[2]};
-      const double tv[3] = {C.Th[0] + C.Tlc[0], C.Th[1] + C.Tlc[1], C.Th[2] + C.Tlc[2]};
+      const double tv[3] = {C.Th[0] + C.Tlc[0] + C.Text[0], C.Th[1] + C.Tlc[1] + C.Text[1],
+                            C.Th[2] + C.Tlc[2] + C.Text[2]};
       double dv[3], dw[3];
       solve_sym3(acc + 12, C.M, fv, dv);
       solve_sym3(acc + 18, C.I, tv, dw);

@@ -251,6 +251,31 @@ def test_two_mobile_colloids_approaching(P, prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_rotating_sedimenting_colloid(P, prec):
+    """A mobile colloid driven by an external force along -z between the walls
+    (sedimentation) and an external torque about z (rotation, surface speed
+    ~0.025) in a cholesteric: translation with re-discretisation and rotation
+    together (Sec. 2.2, last paragraph; Sec. 3.2, closing paragraph), GPU
+    against oracle, links bit-exact."""
+    L = (24, 22, 26)
+    prm = dict(synth.NEMATIC, q0=2 * math.pi / 24)
+    cols = [dict(X=(11.6, 10.3, 16.2), a0=4.2, anchoring=1, w=0.02, mobile=True, F_ext=(0.0, 0.0, -0.5))]
+    g, o = make_pair(P, L, prm, P.LC_FP32 if prec == "f32" else P.LC_FP64, wall_z=True, colloids=cols,
+                     init=("helix", 2, 1e-2, 7))
+    for s in (g, o):
+        s.set_colloid_torque(0, (0.0, 0.0, 5.0))
+    s0 = o.get_solid()
+    g.step(120)
+    o.step(120)
+    assert (o.get_solid() != s0).sum() > 40
+    assert o.colloid(0)["W"][2] > 5e-3 and o.colloid(0)["V"][2] < -5e-3
+    compare(g, o, TOL32 if prec == "f32" else TOL64, ncol=1, radii=[4.2])
+    ng, dg, cg = g.links()
+    no, do, co = o.links()
+    assert (ng == no).all() and (dg == do).all() and (cg == co).all()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_contact_between_colloids_refused_and_reported(P, prec):
     """Two mobile colloids pushed together by external forces until their
     centres come closer than the sum of the radii: that move is not made, on
