@@ -52,6 +52,9 @@ struct Phase {
   size_t part_cap = 0;
 };
 
+// Partial records per tile: the Q update (phase 2) writes one per warp, TY per tile.
+inline int part_records(const Phase& P, int k) { return k == 2 ? P.cfg.ty : 1; }
+
 struct Mem {
   std::vector<std::pair<void*, cudaStream_t>> blocks;
   void* get(size_t bytes, cudaStream_t s, Allocator& al) {
@@ -207,7 +210,7 @@ int build_phase(Group* g, int k) {
   P.d_tiles = (int4*)galloc(g, sizeof(int4) * tl.size());
   if (!P.d_tiles) return fail(&g->err, LC_ERR_OOM, "tile list allocation failed");
   CK(cudaMemcpyAsync(P.d_tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice, g->stream), &g->err);
-  const size_t need = (size_t)PART_WIDTH[k] * tl.size();
+  const size_t need = (size_t)PART_WIDTH[k] * tl.size() * part_records(P, k);
   if (need > P.part_cap) {
     if (P.d_part) g->mem.put(P.d_part, g->al);
     P.d_part = (double*)galloc(g, sizeof(double) * need);
@@ -501,7 +504,8 @@ void tune_file_store(const TuneKey& key, const std::vector<TileCfg>& c) {
 
 cudaError_t launch_phase(Group* g, int k, int mode, int box = -1) {
   Launch L = phase_launch(g, k, box);
-  double* part = g->ph[k].d_part + (box < 0 ? 0 : (size_t)g->ph[k].start[box] * PART_WIDTH[k]);
+  double* part = g->ph[k].d_part +
+                 (box < 0 ? 0 : (size_t)g->ph[k].start[box] * PART_WIDTH[k] * part_records(g->ph[k], k));
   if (k == 0) return launch_force(g->prec, L, mode, part);
   if (k == 1) return launch_lb(g->prec, L, mode, part);
   if (k == 2) return launch_lc(g->prec, L, mode, part);
@@ -1233,7 +1237,8 @@ int group_step(Group* g, int n) {
 // Residual (RMS, max) of the last step of box b -> h_red[0..1] (synchronises).
 int box_residual(Group* g, int b, double* rms, double* mx, long long nfluid) {
   Phase& P = g->ph[2];
-  CK(launch_reduce(P.d_part, P.start[b], P.count[b], 2, 2u, g->d_red, g->stream), &g->err);
+  const int rec = part_records(P, 2);
+  CK(launch_reduce(P.d_part, P.start[b] * rec, P.count[b] * rec, 2, 2u, g->d_red, g->stream), &g->err);
   CK(cudaMemcpyAsync(g->h_red, g->d_red, 2 * sizeof(double), cudaMemcpyDeviceToHost, g->stream), &g->err);
   CK(cudaStreamSynchronize(g->stream), &g->err);
   *rms = nfluid > 0 ? std::sqrt(g->h_red[0] / (double)nfluid) : 0.0;

@@ -67,6 +67,23 @@ __device__ void block_sum(double v[NV], double* sred, bool is_max_last = false) 
   __syncthreads();
 }
 
+// Residual partials of a warp's row of a Q-update tile: the sum of squares
+// and the max over its lanes, written by lane 0 to part[2 wy], part[2 wy + 1]
+// (one record per warp, so a tile needs no block barrier and no FP64 sum).
+template <typename T>
+__device__ __forceinline__ void warp_residual(double* part, int wy, int lane, T rsum, T rmax) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rsum += __shfl_down_sync(0xffffffffu, rsum, o);
+    const T m = __shfl_down_sync(0xffffffffu, rmax, o);
+    rmax = m > rmax ? m : rmax;
+  }
+  if (lane == 0) {
+    part[2 * wy] = (double)rsum;
+    part[2 * wy + 1] = (double)rmax;
+  }
+}
+
 // Add per-lane contributions v[0..5] (for colloid id c, -1: none) into
 // acc[off..off+NV-1] of each colloid with one FP64 atomic per (warp, colloid,
 // component).  Must be called by all 32 lanes of a converged warp.
@@ -1187,12 +1204,11 @@ __device__ __forceinline__ void lc_update_node(const DevBox& B, const PhysT<T>& 
 
 // k_lc: Beris-Edwards update; plain nodes of a warp's row together, nodes
 // next to a solid or wall queued and updated 32 at a time.  part (if non-null)
-// receives the tile's residual partials (sum of squares, max).
+// receives the tile's residual partials (sum of squares, max), one record per
+// warp (TY records per tile).
 template <typename T, int TY, bool CG>
-__device__ __forceinline__ void lc_tile(const DevBox& B, const int4 td, int zc, double* part, double* sred,
-                                        int (*sq)[2 * TX]) {
+__device__ __forceinline__ void lc_tile(const DevBox& B, const int4 td, int zc, double* part, int (*sq)[2 * TX]) {
   if (!B.p.lc_on) return;
-  const int tid = threadIdx.x + TX * threadIdx.y;
   const int lane = threadIdx.x, wy = threadIdx.y;
   const int qpar = B.st->qpar;
   const T* __restrict__ Q = static_cast<const T*>(B.Q[qpar]);
@@ -1249,14 +1265,7 @@ __device__ __forceinline__ void lc_tile(const DevBox& B, const int4 td, int zc, 
                                 rmax);
   }
   __syncwarp();
-  if (part) {
-    double rs[2] = {(double)rsum, (double)rmax};
-    block_sum<2>(rs, sred, true);
-    if (tid == 0) {
-      part[0] = rs[0];
-      part[1] = rs[1];
-    }
-  }
+  if (part) warp_residual<T>(part, wy, lane, rsum, rmax);
 }
 
 // Q update, two nodes per lane (FP32 boxes of even width; tiles 64 wide): the
@@ -1388,10 +1397,9 @@ __device__ __forceinline__ void lc_update_pair(const DevBox& B, float* __restric
 }
 
 template <int TY, bool CG>
-__device__ __forceinline__ void lc_tile_pair(const DevBox& B, const int4 td, int zc, double* part, double* sred,
+__device__ __forceinline__ void lc_tile_pair(const DevBox& B, const int4 td, int zc, double* part,
                                              int (*sq)[2 * TX]) {
   if (!B.p.lc_on) return;
-  const int tid = threadIdx.x + TX * threadIdx.y;
   const int lane = threadIdx.x, wy = threadIdx.y;
   const int qpar = B.st->qpar;
   const float* __restrict__ Q = static_cast<const float*>(B.Q[qpar]);
@@ -1455,14 +1463,7 @@ __device__ __forceinline__ void lc_tile_pair(const DevBox& B, const int4 td, int
   }
   if (lane < nq) near_fn(sq[wy][lane]);
   __syncwarp();
-  if (part) {
-    double rs[2] = {(double)rsum, (double)rmax};
-    block_sum<2>(rs, sred, true);
-    if (tid == 0) {
-      part[0] = rs[0];
-      part[1] = rs[1];
-    }
-  }
+  if (part) warp_residual<float>(part, wy, lane, rsum, rmax);
 }
 
 template <typename T, int TY>
@@ -1470,19 +1471,19 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 : 256) / (TX * 
     const DevBox* __restrict__ boxes, const int4* __restrict__ tiles, int ntiles, int zc, int mode,
     double* __restrict__ part) {
   __shared__ DevBox B;
-  __shared__ double sred[32 * 2];
   __shared__ int sq[TY][2 * TX];
   int cur_box = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int4 td = tiles[t];
     load_box(B, boxes, td.x, cur_box);
+    double* pt = (mode & LC_RESID) ? part + 2 * (size_t)t * TY : nullptr;
     if constexpr (sizeof(T) == 4) {
       if (pair_box(B)) {
-        lc_tile_pair<TY, false>(B, td, zc, (mode & LC_RESID) ? part + 2 * t : nullptr, sred, sq);
+        lc_tile_pair<TY, false>(B, td, zc, pt, sq);
         continue;
       }
     }
-    lc_tile<T, TY, false>(B, td, zc, (mode & LC_RESID) ? part + 2 * t : nullptr, sred, sq);
+    lc_tile<T, TY, false>(B, td, zc, pt, sq);
   }
 }
 
@@ -1771,7 +1772,6 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 : 256) / (TX * 
     DevBox* __restrict__ boxes, const StepItem* __restrict__ items, int nitems, int zc, unsigned* __restrict__ sync,
     double* __restrict__ part, int spin_limit, int commit, int* __restrict__ err) {
   __shared__ DevBox B;
-  __shared__ double sred[32 * 2];
   __shared__ double sblk[18];
   __shared__ int sq[TY][2 * TX];
   __shared__ int s_item, s_ok, s_sc0;
@@ -1819,11 +1819,11 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 : 256) / (TX * 
         case ITEM_LC:
           if constexpr (sizeof(T) == 4) {
             if (pair_box(B)) {
-              lc_tile_pair<TY, true>(B, td, zc, part + 2 * (size_t)I.part, sred, sq);
+              lc_tile_pair<TY, true>(B, td, zc, part + 2 * (size_t)I.part * TY, sq);
               break;
             }
           }
-          lc_tile<T, TY, true>(B, td, zc, part + 2 * (size_t)I.part, sred, sq);
+          lc_tile<T, TY, true>(B, td, zc, part + 2 * (size_t)I.part * TY, sq);
           break;
         case ITEM_LINKS: links_chunk<T, true>(B, I.x0, LINK_CHUNK, sblk, &s_sc0); break;
         default: colloid_box<true>(B, commit != 0); break;
