@@ -240,13 +240,21 @@ def run_reference(args, ws, rank):
     o.step(args.steps)
     dt = time.perf_counter() - t0
     v = L**3 * args.steps / dt / 1e6
+    full = synth.workload(args.workload)
+    c0 = full["colloids"][0]
+    sample = (f"{args.steps} steps of a {L}^3 box with the same constants, initial field and colloid at its "
+              f"centre (a bounded sample of the {'x'.join(map(str, full['grid']))} workload), {cores} threads")
     out = dict(metric=METRIC, value=v, unit="MLUPS", n_gpus=ws, steps=args.steps, warmup=args.warmup,
                ms_per_step=1e3 * dt / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
                dtype="f64", data="synthetic", impl="reference",
-               config=dict(workload=f"{args.workload} (bounded sample: {L}^3 box, same constants and colloid)",
-                           parallelism="host cores"),
-               cpu_baseline=dict(value=v, unit="MLUPS", cores=cores, kind="oracle",
-                                 sample=f"{args.steps} steps of a {L}^3 sample of {args.workload}, {cores} threads"),
+               config=dict(workload=args.workload, grid=list(full["grid"]),
+                           nodes=full["grid"][0] * full["grid"][1] * full["grid"][2],
+                           colloid=dict(R=c0["a0"], anchoring="normal" if c0["anchoring"] == 0 else "planar",
+                                        w=c0["w"]),
+                           pitch=round(2 * 3.141592653589793 / full["params"]["q0"], 6) if full["params"]["q0"]
+                           else None, parallelism="host cores"),
+               sample=sample,
+               cpu_baseline=dict(value=v, unit="MLUPS", cores=cores, kind="oracle", sample=sample),
                e2e=dict(value=v, unit="MLUPS", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(out), flush=True)
     return 0
@@ -293,6 +301,41 @@ def batch_line(steps, local):
                                   bytes_per_node=STEP_BYTES))
     B.close()
     return out
+
+
+def warm_line(local):
+    """Short plain-vs-warm time to residual (the relaxation half of the metric):
+    a U-Net trained on 16 seeded 32^3 cholesteric boxes relaxed by the lattice
+    method proposes the start of a held-out box, which is then relaxed to an
+    RMS residual of 1e-7 from that proposal and from the helix (the paper's
+    constants, flow frozen, FP32 storage; residual tested every 250 steps).
+    A short relaxation of the same box first takes the autotuning and graph
+    capture out of both timings.  Wall times include the network's inference;
+    dataset and training times are reported apart."""
+    import torch
+
+    from paper_1102_2193_gb300 import warmstart as wst
+    from paper_1102_2193_gb300.surrogate import UNet
+    S, tol = 32, 1e-7
+    specs = wst.commensurate_geometries(17, S, seed=2024)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    data = wst.relaxed_dataset(specs[:16], S, 20000, torch, tol=tol)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = UNet(S=S, seed=3)
+    t1 = time.perf_counter()
+    wst.train(net, data, epochs=8)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    wst.relax_from(specs[16], S, None, tol, None, torch, max_steps=500, check=250)
+    r = wst.compare(net, specs[16], S, torch, tol_fp32=tol, max_steps=200000, check=250)
+    pl, wm = r["plain"], r["warm"]
+    return dict(workload=f"warm{S}", S=S, R=specs[16]["R"], pitch=specs[16]["pitch"], w=specs[16]["w"], tol=tol,
+                plain=dict(steps=pl["steps_fp32"], s=pl["time"], resid=pl["resid"]),
+                warm=dict(steps=wm["steps_fp32"], s=wm["time"], resid=wm["resid"], inference_s=wm["time_propose"]),
+                speedup_steps=r["speedup_steps"], speedup_time=r["speedup_time"], free_energy_rel=r["free_energy_rel"],
+                warm_accepted=r["warm_accepted"], train_boxes=len(data), dataset_s=t_data, train_s=t_train)
 
 
 def run_batch(args, ws, rank, local):
@@ -418,6 +461,9 @@ def run_gpu(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_batch:
         del s
         batched = batch_line(args.batch_steps, local)
+    warm = None
+    if rank == 0 and ws == 1 and not args.no_warm:
+        warm = warm_line(local)
 
     if rank == 0:
         out = dict(
@@ -443,7 +489,7 @@ def run_gpu(args, ws, rank, local):
                                frac=step_gbs / peaks["hbm"], bytes_per_node=STEP_BYTES,
                                note="whole coupled step: 192 B/node algorithmic (df + Q, read + write)"),
             phase_ms=prof, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches_per_step * args.steps,
-            launches_per_step=launches_per_step, clocks=clocks, batched64=batched)
+            launches_per_step=launches_per_step, clocks=clocks, batched64=batched, warm_vs_plain=warm)
         print(json.dumps(out), flush=True)
     if dist:
         torch.distributed.destroy_process_group()
@@ -461,6 +507,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep sub-object")
     ap.add_argument("--batch-steps", type=int, default=300)
+    ap.add_argument("--no-warm", action="store_true", help="skip the warm-vs-plain relaxation sub-object")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

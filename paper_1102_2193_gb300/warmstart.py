@@ -180,17 +180,19 @@ def relax_from(spec, S, q_start, tol_fp32, tol, torch, max_steps=2_000_000, chec
     return out
 
 
-def compare(net: UNet, spec, S, torch, tol_fp32=1e-8, tol=None, max_steps=2_000_000, mode="direct", plain=None):
+def compare(net: UNet, spec, S, torch, tol_fp32=1e-8, tol=None, max_steps=2_000_000, mode="direct", plain=None,
+            check=1000):
     """Relax from the helix (``plain``, when given, is a result of an earlier
-    relaxation of the same case) and from the network's proposal."""
+    relaxation of the same case) and from the network's proposal, testing the
+    residual every ``check`` steps."""
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     q_warm = propose(net, spec, S, torch, mode)
     torch.cuda.synchronize()
     t_propose = time.perf_counter() - t0
     if plain is None:
-        plain = relax_from(spec, S, None, tol_fp32, tol, torch, max_steps)
-    warm = relax_from(spec, S, q_warm, tol_fp32, tol, torch, max_steps)
+        plain = relax_from(spec, S, None, tol_fp32, tol, torch, max_steps, check)
+    warm = relax_from(spec, S, q_warm, tol_fp32, tol, torch, max_steps, check)
     warm["time_propose"] = t_propose  # network inference is part of the warm start's wall time
     warm["time"] += t_propose
     use_warm = warm["free_energy"] <= plain["free_energy"] + 1e-4 * abs(plain["free_energy"])
