@@ -34,9 +34,14 @@ int lc_nn_conv3d_fwd(const void* in, const void* w, const float* bias, float* ou
 int lc_nn_conv3d_dgrad(const void* dout, const void* w, void* wt_scratch, float* din32, void* din16, int W, int H,
                        int D, int cin, int cout, int taps, void* stream);
 /* Weight gradient, accumulated: dw[co][t][ci] += sum_p dout[p][co] in[p + offset(t)][ci]
- * (dw FP32, cout % 16 == 0, cin % 8 == 0, cin <= 80). */
-int lc_nn_conv3d_wgrad(const void* dout, const void* in, float* dw, int W, int H, int D, int cin, int cout, int taps,
-                       void* stream);
+ * (dw FP32, cout % 16 == 0, cin % 8 == 0, cin <= 80).  The positions are
+ * split into at most 256 chunks whose partial sums go to `partial` (caller
+ * memory of lc_nn_wgrad_partial_floats(...) floats) and are then added in
+ * chunk order, so the result is the same on every run.  Errors: LC_NN_ERR_ARG. */
+int lc_nn_conv3d_wgrad(const void* dout, const void* in, float* dw, float* partial, int W, int H, int D, int cin,
+                       int cout, int taps, void* stream);
+/* Size in floats of the partial-sum buffer of lc_nn_conv3d_wgrad. */
+size_t lc_nn_wgrad_partial_floats(int W, int H, int D, int cin, int cout, int taps);
 /* db[c] += sum_p dout[p][c]. */
 int lc_nn_bias_grad(const float* dout, float* db, int npos, int c, void* stream);
 /* dz = dy * (y > 0) for n elements; dz32 (FP32) and/or dz16 (BF16). */

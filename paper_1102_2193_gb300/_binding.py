@@ -164,7 +164,9 @@ def lib(use_torch_allocator: bool = True):
         L.lc_nn_conv3d_fwd.argtypes = [vp, vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                        C.c_int, vp]
         L.lc_nn_conv3d_dgrad.argtypes = [vp, vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
-        L.lc_nn_conv3d_wgrad.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+        L.lc_nn_conv3d_wgrad.argtypes = [vp, vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+        L.lc_nn_wgrad_partial_floats.argtypes = [C.c_int] * 6
+        L.lc_nn_wgrad_partial_floats.restype = C.c_size_t
         L.lc_nn_bias_grad.argtypes = [vp, vp, C.c_int, C.c_int, vp]
         L.lc_nn_relu_bwd.argtypes = [vp, vp, vp, vp, C.c_size_t, vp]
         L.lc_nn_cast_bf16.argtypes = [vp, vp, C.c_size_t, vp]

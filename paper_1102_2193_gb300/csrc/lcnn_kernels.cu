@@ -99,12 +99,13 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const __nv_bfloat16* __restric
   }
 }
 
-// dW[co][t][ci] += sum_p dout[p][co] in[tap(p, t)][ci] over one chunk of
-// positions; one warp per (chunk, tap, 16 output channels).  A = dout^T
-// (16 C_out x 16 positions), B = shifted input (16 positions x 8 C_in).
+// Partial dW[co][t][ci] = sum_p dout[p][co] in[tap(p, t)][ci] over one chunk
+// of positions, stored for the chunk (part[chunk][co][t][ci]); one warp per
+// (chunk, tap, 16 output channels).  A = dout^T (16 C_out x 16 positions),
+// B = shifted input (16 positions x 8 C_in).
 template <int NTI>
 __global__ void __launch_bounds__(32) k_conv_wgrad(const __nv_bfloat16* __restrict__ dout,
-                                                   const __nv_bfloat16* __restrict__ in, float* __restrict__ dw,
+                                                   const __nv_bfloat16* __restrict__ in, float* __restrict__ part,
                                                    int npos, int W, int H, int D, int cin, int cout, int taps,
                                                    int chunk) {
   const int lane = threadIdx.x, g = lane >> 2, tg = lane & 3;
@@ -138,13 +139,23 @@ __global__ void __launch_bounds__(32) k_conv_wgrad(const __nv_bfloat16* __restri
       mma_bf16(acc[j], a, b);
     }
   }
+  float* dw = part + (size_t)blockIdx.x * cout * taps * cin;
 #pragma unroll
   for (int j = 0; j < NTI; ++j) {
     const int ci = j * 8 + tg * 2;
-    atomicAdd(&dw[((size_t)(co0 + g) * taps + t) * cin + ci], acc[j][0]);
-    atomicAdd(&dw[((size_t)(co0 + g) * taps + t) * cin + ci + 1], acc[j][1]);
-    atomicAdd(&dw[((size_t)(co0 + g + 8) * taps + t) * cin + ci], acc[j][2]);
-    atomicAdd(&dw[((size_t)(co0 + g + 8) * taps + t) * cin + ci + 1], acc[j][3]);
+    dw[((size_t)(co0 + g) * taps + t) * cin + ci] = acc[j][0];
+    dw[((size_t)(co0 + g) * taps + t) * cin + ci + 1] = acc[j][1];
+    dw[((size_t)(co0 + g + 8) * taps + t) * cin + ci] = acc[j][2];
+    dw[((size_t)(co0 + g + 8) * taps + t) * cin + ci + 1] = acc[j][3];
+  }
+}
+
+// dw[e] += sum over the chunks, in chunk order, of part[chunk][e].
+__global__ void k_wgrad_sum(const float* __restrict__ part, float* __restrict__ dw, int nchunk, size_t nw) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nw; e += (size_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * nw + e];
+    dw[e] += s;
   }
 }
 
@@ -458,23 +469,42 @@ int lc_nn_conv3d_dgrad(const void* dout, const void* w, void* wt_scratch, float*
   return lc_nn_conv3d_fwd(dout, wt_scratch, nullptr, din32, din16, W, H, D, cout, cin, taps, 0, stream);
 }
 
-int lc_nn_conv3d_wgrad(const void* dout, const void* in, float* dw, int W, int H, int D, int cin, int cout, int taps,
-                       void* stream) {
-  if (!dout || !in || !dw || cout % 16 || cin % 8 || cin > 80) return LC_NN_ERR_ARG;
+// Positions per chunk of the weight gradient: 1024, more when that would give
+// more than 256 chunks (a multiple of 16, the MMA's K).
+static int wgrad_chunk(int npos) {
+  int chunk = 1024;
+  while ((npos + chunk - 1) / chunk > 256) chunk *= 2;
+  return chunk;
+}
+
+size_t lc_nn_wgrad_partial_floats(int W, int H, int D, int cin, int cout, int taps) {
   const int npos = W * H * D;
-  const int chunk = 1024;
-  const dim3 grid((npos + chunk - 1) / chunk, taps, cout / 16);
+  if (npos <= 0) return 0;
+  const int nchunk = (npos + wgrad_chunk(npos) - 1) / wgrad_chunk(npos);
+  return (size_t)nchunk * cout * taps * cin;
+}
+
+int lc_nn_conv3d_wgrad(const void* dout, const void* in, float* dw, float* partial, int W, int H, int D, int cin,
+                       int cout, int taps, void* stream) {
+  if (!dout || !in || !dw || !partial || cout % 16 || cin % 8 || cin > 80) return LC_NN_ERR_ARG;
+  const int npos = W * H * D;
+  if (npos <= 0) return LC_NN_ERR_ARG;
+  const int chunk = wgrad_chunk(npos);
+  const int nchunk = (npos + chunk - 1) / chunk;
+  const dim3 grid(nchunk, taps, cout / 16);
   cudaStream_t s = (cudaStream_t)stream;
   auto* a = (const __nv_bfloat16*)dout;
   auto* b = (const __nv_bfloat16*)in;
   switch (cin / 8) {
-    case 1: k_conv_wgrad<1><<<grid, 32, 0, s>>>(a, b, dw, npos, W, H, D, cin, cout, taps, chunk); break;
-    case 2: k_conv_wgrad<2><<<grid, 32, 0, s>>>(a, b, dw, npos, W, H, D, cin, cout, taps, chunk); break;
-    case 4: k_conv_wgrad<4><<<grid, 32, 0, s>>>(a, b, dw, npos, W, H, D, cin, cout, taps, chunk); break;
-    case 6: k_conv_wgrad<6><<<grid, 32, 0, s>>>(a, b, dw, npos, W, H, D, cin, cout, taps, chunk); break;
-    case 10: k_conv_wgrad<10><<<grid, 32, 0, s>>>(a, b, dw, npos, W, H, D, cin, cout, taps, chunk); break;
+    case 1: k_conv_wgrad<1><<<grid, 32, 0, s>>>(a, b, partial, npos, W, H, D, cin, cout, taps, chunk); break;
+    case 2: k_conv_wgrad<2><<<grid, 32, 0, s>>>(a, b, partial, npos, W, H, D, cin, cout, taps, chunk); break;
+    case 4: k_conv_wgrad<4><<<grid, 32, 0, s>>>(a, b, partial, npos, W, H, D, cin, cout, taps, chunk); break;
+    case 6: k_conv_wgrad<6><<<grid, 32, 0, s>>>(a, b, partial, npos, W, H, D, cin, cout, taps, chunk); break;
+    case 10: k_conv_wgrad<10><<<grid, 32, 0, s>>>(a, b, partial, npos, W, H, D, cin, cout, taps, chunk); break;
     default: return LC_NN_ERR_ARG;
   }
+  const size_t nw = (size_t)cout * taps * cin;
+  k_wgrad_sum<<<grid_for(nw), 256, 0, s>>>(partial, dw, nchunk, nw);
   return cudaGetLastError() == cudaSuccess ? LC_NN_OK : LC_NN_ERR_CUDA;
 }
 

@@ -90,6 +90,10 @@ class UNet:
         self.nf = 0.0
         self.dy = f32(0, 16)  # gradient of the loss w.r.t. the head output
         self.dskip = {"c0b": f32(0, 16), "c1b": f32(1, 32)}
+        # partial sums of the weight gradients (deterministic, summed in chunk order)
+        nwp = max(self.L.lc_nn_wgrad_partial_floats(S >> lvl, S >> lvl, S >> lvl, cin, cout, taps)
+                  for _, cin, cout, taps, _, lvl in LAYERS)
+        self.wpart = t.empty(nwp, dtype=t.float32, device=self.dev)
 
     def _cast(self, a, b):
         _ok(self.L.lc_nn_cast_bf16(_p(a), _p(b), a.numel(), self.sp), "cast")
@@ -171,7 +175,8 @@ class UNet:
         else:
             dz32 = dout32
             self._cast(dout32, dz16)
-        _ok(L.lc_nn_conv3d_wgrad(_p(dz16), _p(src), _p(P["gw"]), W, H, D, cin, cout, taps, sp), "wgrad")
+        _ok(L.lc_nn_conv3d_wgrad(_p(dz16), _p(src), _p(P["gw"]), _p(self.wpart), W, H, D, cin, cout, taps, sp),
+            "wgrad")
         _ok(L.lc_nn_bias_grad(_p(dz32), _p(P["gb"]), n, cout, sp), "bias_grad")
         if need_din:
             _ok(L.lc_nn_conv3d_dgrad(_p(dz16), _p(P["w16"]), _p(P["wt"]), _p(din32), None, W, H, D, cin, cout, taps,
