@@ -5,9 +5,10 @@ Nematic along z between homeotropic no-slip walls, one mobile planar colloid
 of radius 8 pulled by 1e-4 across (x) or along (z) the director (Sec. 3.1,
 Eq. 9); samples every 1000 steps.
 
-FP64 storage (first 4000 steps): the colloid's velocity, both force parts
-and the total force within 1e-9 relative of the oracle -- the same method to
-round-off, and inside the 1e-4 force tolerance with room to spare.
+FP64 storage (all 20 000 steps): the colloid's velocity, both force parts
+and the total force within 1e-9 relative of the oracle at every sample -- the
+same method to round-off, and inside the 1e-4 force tolerance with room to
+spare.
 
 FP32 storage (all 20 000 steps; Q kept as FP32 plus a BF16 remainder so that
 no part of the ~1e-7 increments is lost to rounding): the colloid's total
@@ -102,8 +103,8 @@ def test_micro64_colloid_trajectory_fp32(run, axis):
 
 
 def test_micro64_colloid_trajectory_fp64():
-    """Both pulls in FP64 storage for the first 4000 steps: the oracle's
-    trajectory to round-off."""
+    """Both pulls in FP64 storage over the whole 20 000 steps: the oracle's
+    trajectory to round-off at every sample."""
     import paper_1102_2193_gb300 as P
     from paper_1102_2193_gb300.microrheology import micro_batch
     w = synth.workload("micro64")
@@ -114,8 +115,9 @@ def test_micro64_colloid_trajectory_fp64():
                     walls=w["wall_z"], params=w["params"], precision=P.LC_FP64, amp=w["init"]["amp"],
                     seed=w["init"]["seed"])
     series = {"x": [], "z": []}
+    nsamp = len(ref["x"]["series"])
     try:
-        for _ in range(4):
+        for _ in range(nsamp):
             B.step(every)
             for a, box in zip(("x", "z"), B.boxes):
                 series[a].append(box.colloid(0))
@@ -123,7 +125,7 @@ def test_micro64_colloid_trajectory_fp64():
         B.close()
     X0 = np.array(c["X"])
     for a in ("x", "z"):
-        errs = _errors(series[a], ref[a]["series"][:4], X0)
+        errs = _errors(series[a], ref[a]["series"][:nsamp], X0)
         worst = {k: max(e[k] for e in errs) for k in errs[0] if k != "X"}
         assert all(v <= TOL["F64"] for v in worst.values()), (a, worst)
 
