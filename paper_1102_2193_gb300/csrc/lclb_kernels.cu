@@ -30,6 +30,32 @@ __device__ __forceinline__ T ldx(const T* p) {
   else return __ldg(p);
 }
 
+// L2 eviction priorities (PTX createpolicy, cache hints on the loads and
+// stores; no setting of the device changes): the stress, molecular field and
+// velocity that the next kernels of the step read are stored to stay
+// (evict_last), the populations, read and written once per step, to go first
+// (evict_first), so the 129 MB L2 keeps the intermediates between kernels.
+__device__ __forceinline__ uint64_t l2_keep() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_stream() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void st_hint(float* a, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint(double* a, double v, uint64_t) { *a = v; }
+__device__ __forceinline__ float ld_hint(const float* a, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double ld_hint(const double* a, uint64_t) { return __ldg(a); }
+
 // ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
@@ -309,10 +335,11 @@ __device__ __forceinline__ void pull(const DevBox& B, const T* __restrict__ fin,
     zs[0] = z == 0 ? nz - 1 : z - 1; zs[1] = z; zs[2] = z + 1 == nz ? 0 : z + 1;
   }
   if (!(m & NEAR)) {
+    const uint64_t pol = l2_stream();
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       const int s = xs[1 - cx(q)] + nx * (ys[1 - cy(q)] + ny * zs[1 - cz(q)]);
-      df[q] = ldg(fin + (size_t)q * N + s);
+      df[q] = ld_hint(fin + (size_t)q * N + s, pol);
     }
     return;
   }
@@ -364,6 +391,7 @@ __device__ __forceinline__ void collide_store(const PhysT<T>& PP, T* __restrict_
   const T usq = ux * ux + uy * uy + uz * uz;
   const T uF = ux * Fx + uy * Fy + uz * Fz;
   const T omega = PP.omega, pref = PP.pref;
+  const uint64_t pol_stream = l2_stream(), pol_keep = l2_keep();
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     const T w = T(wq(q));
@@ -371,11 +399,11 @@ __device__ __forceinline__ void collide_store(const PhysT<T>& PP, T* __restrict_
     const T cF = T(cx(q)) * Fx + T(cy(q)) * Fy + T(cz(q)) * Fz;
     const T eq = w * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
     const T src = pref * w * (T(3) * (cF - uF) + T(9) * cu * cF);
-    fout[(size_t)q * N + i] = df[q] - omega * (df[q] - eq) + src;
+    st_hint(fout + (size_t)q * N + i, df[q] - omega * (df[q] - eq) + src, pol_stream);
   }
-  ub[i] = ux;
-  ub[(size_t)N + i] = uy;
-  ub[(size_t)2 * N + i] = uz;
+  st_hint(ub + i, ux, pol_keep);
+  st_hint(ub + (size_t)N + i, uy, pol_keep);
+  st_hint(ub + (size_t)2 * N + i, uz, pol_keep);
 }
 
 template <typename T>
@@ -663,6 +691,10 @@ __device__ __forceinline__ void stress_tile(const DevBox& B, const int4 td, int 
 // per-warp queue of the one-node path.
 __device__ __forceinline__ f2 ld2(const float* p) { return f2(__ldg(reinterpret_cast<const float2*>(p))); }
 __device__ __forceinline__ void st2(float* p, f2 v) { *reinterpret_cast<float2*>(p) = v.v; }
+__device__ __forceinline__ void st2_keep(float* p, f2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.v.x), "f"(v.v.y), "l"(pol)
+               : "memory");
+}
 
 template <bool CG>
 __device__ __forceinline__ f2 ldx2(const float* p) {
@@ -779,10 +811,11 @@ __device__ __forceinline__ void stress_tile_pair(const DevBox& B, const int4 td,
       f2 dq[3][5], lap[5], h[5], p[9], fp;
       derivatives(qz[1], qn, dq, lap);
       lc_node_d<f2, true, float>(B.pf, qz[1], dq, lap, h, p, &fp);
+      const uint64_t keep = l2_keep();
 #pragma unroll
-      for (int c = 0; c < 5; ++c) st2(Hb + c * N + i, h[c]);
+      for (int c = 0; c < 5; ++c) st2_keep(Hb + c * N + i, h[c], keep);
 #pragma unroll
-      for (int c = 0; c < 9; ++c) st2(Pb + c * N + i, p[c]);
+      for (int c = 0; c < 9; ++c) st2_keep(Pb + c * N + i, p[c], keep);
     }
     queue_push(sq, wy, lane, nq, fA && !plain, i, near_fn);
     queue_push(sq, wy, lane, nq, fB && !plain, i + 1, near_fn);
