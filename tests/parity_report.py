@@ -36,6 +36,20 @@ def cases(P):
         yield ("moving colloid, re-discretisation, 120 steps", prec, (24, 20, 18), dict(synth.NEMATIC), False,
                [dict(X=(11.3, 9.6, 8.8), a0=3.6, anchoring=1, w=0.02, mobile=True)],
                ("uniaxial", (0, 0, 1), 1e-2, 3), 120, (0.02, -0.01, 0.015))
+    chol20 = dict(synth.NEMATIC, q0=2 * math.pi / 20)
+    chol24 = dict(synth.NEMATIC, q0=2 * math.pi / 24)
+    for prec in ("f32", "f64"):
+        yield ("two mobile colloids approaching (normal strong, planar weak), 100 steps", prec, (28, 22, 20), chol20,
+               False, [dict(X=(8.3, 10.6, 9.2), a0=3.5, anchoring=0, w=float("inf"), mobile=True),
+                       dict(X=(19.1, 10.9, 9.9), a0=3.0, anchoring=1, w=0.02, mobile=True)],
+               ("helix", 2, 1e-2, 5), 100, [((0.02, 0.0, 0.003), None), ((-0.02, 0.002, 0.0), None)])
+        yield ("rotating, sedimenting colloid between walls (F_ext, T_ext), 120 steps", prec, (24, 22, 26), chol24,
+               True, [dict(X=(11.6, 10.3, 16.2), a0=4.2, anchoring=1, w=0.02, mobile=True, F_ext=(0.0, 0.0, -0.5))],
+               ("helix", 2, 1e-2, 7), 120, [(None, (0.0, 0.0, 5.0))])
+        yield ("colliding pair, contact refused and reported, 60 steps", prec, (28, 22, 20), chol20, False,
+               [dict(X=(9.3, 10.6, 9.2), a0=3.5, anchoring=0, w=float("inf"), mobile=True, F_ext=(1.2, 0.0, 0.0)),
+                dict(X=(16.8, 10.9, 9.9), a0=3.0, anchoring=1, w=0.02, mobile=True, F_ext=(-1.2, 0.0, 0.0))],
+               ("helix", 2, 1e-2, 5), 60, None)
     yield ("128^3 cholesteric R = 8 (bench workload), 3 steps", "f32", w128["grid"], w128["params"], False,
            [w128["colloids"][0]], ("helix", 2, w128["init"]["amp"], w128["init"]["seed"]), 3, None)
 
@@ -53,11 +67,23 @@ def main():
     for name, prec, L, prm, wall, cols, init, steps, vel in cases(P):
         g, o = make_pair(P, L, prm, P.LC_FP32 if prec == "f32" else P.LC_FP64, wall_z=wall, colloids=cols,
                          init=init, threads=16)
-        if vel is not None:
+        # vel: the first colloid's velocity, or per colloid a (velocity, external torque) pair
+        if isinstance(vel, list):
+            for c, (V, T) in enumerate(vel):
+                for s in (g, o):
+                    if V is not None:
+                        s.set_colloid_velocity(c, V)
+                    if T is not None:
+                        s.set_colloid_torque(c, T)
+        elif vel is not None:
             g.set_colloid_velocity(0, vel)
             o.set_colloid_velocity(0, vel)
         g.step(steps)
         o.step(steps)
+        try:
+            g.synchronize()
+        except P.LcLbError as e:  # a refused contact: reported once, the state stays valid
+            assert e.code == P.LC_ERR_OVERLAP and o.contact() is not None, e
         rep = {}
         compare(g, o, TOL32 if prec == "f32" else TOL64, ncol=len(cols), report=rep, radii=[c["a0"] for c in cols])
         fr = max(v for k, v in rep.items() if k.startswith("force") and k.endswith("_rel"))
