@@ -322,6 +322,34 @@ def test_wall_contact_refused_and_reported(P, prec):
     assert g.colloid(0)["X"][2] - 3.5 >= -0.5
 
 
+def test_contact_in_a_batch_names_its_box(P):
+    """In a batch the contact of one box is reported, with that box's index,
+    by the next synchronising call on any box of the batch, once; the other
+    box steps on unaffected (it matches its single-box run to FP32 rounding)."""
+    prm = dict(synth.NEMATIC, q0=2 * math.pi / 20)
+    L = (28, 22, 20)
+    B = P.Batch([dict(grid=L, params=prm), dict(grid=L, params=prm)], precision=P.LC_FP32)
+    single = P.Solver(*L, precision=P.LC_FP32, **prm)
+    try:
+        for s in (B.boxes[0], single):
+            s.init_helix(2, 1e-2, 5)
+            s.add_colloid((9.3, 10.6, 9.2), 3.5, P.LC_NORMAL)
+        box = B.boxes[1]
+        box.init_helix(2, 1e-2, 5)
+        box.add_colloid((9.3, 10.6, 9.2), 3.5, P.LC_NORMAL, float("inf"), True, (1.2, 0.0, 0.0))
+        box.add_colloid((16.8, 10.9, 9.9), 3.0, P.LC_PLANAR, 0.02, True, (-1.2, 0.0, 0.0))
+        B.step(60)
+        single.step(60)
+        with pytest.raises(P.LcLbError) as e:
+            B.boxes[0].colloid(0)
+        assert e.value.code == P.LC_ERR_OVERLAP and "of box 1 would touch colloid 1;" in str(e.value), str(e.value)
+        B.boxes[0].colloid(0)  # reported once
+        np.testing.assert_allclose(B.boxes[0].get_Q(), single.get_Q(), atol=1e-6)
+    finally:
+        single.close()
+        B.close()
+
+
 def test_add_rejects_touching_colloid_with_no_shared_node(P):
     g = P.Solver(16, 12, 12)
     g.add_colloid((5.5, 5.5, 5.5), 0.6)  # holds no node
