@@ -476,7 +476,8 @@ def run_gpu(args, ws, rank, local):
                         pitch=round(2 * 3.141592653589793 / w["params"]["q0"], 6) if w["params"]["q0"] else None,
                         storage="FP32 (df deviation, Q) with FP64 reductions",
                         l2="inputs larger than L2 (state ~0.45 GB per box); no flush", parallelism=f"replicas x{ws}"),
-            roofline=dict(kernel=f"{kname} ({KERNEL_DESC[kname]})", bound="hbm",
+            roofline=dict(scope="the dominant kernel of the step (the whole step: step_roofline)",
+                          kernel=f"{kname} ({KERNEL_DESC[kname]})", bound="hbm",
                           achieved=achieved, peak=peaks["hbm"], unit="GB/s", frac=achieved / peaks["hbm"],
                           traffic=traffic, bytes_per_node=KERNEL_ALGO_BYTES[kname], units_per_launch=N,
                           launch_ms=kms, peak_source=f"{peaks['src']} hbm_gbs (burst copy)",
