@@ -321,3 +321,58 @@ def test_moving_colloid_rediscretisation_conserves_momentum():
                                        rtol=1e-10, atol=1e-16)
         np.testing.assert_allclose(o.diag()["momentum"] + after["impulse"], p0, atol=1e-13)
     assert changes >= 3  # the solid set did change
+
+
+def test_uncovered_nodes_take_neighbour_means_and_equilibrium():
+    """Sec. 2.2, last paragraph: a node that a moving colloid uncovers gets
+    the mean Q of its face neighbours that are fluid before and after the move
+    (Q written out in full, so the mean is of the traceless tensors), and
+    equilibrium populations at their mean density moving with the colloid's
+    surface: its f is the D3Q19 equilibrium of its own moments, its density
+    is that mean, and its velocity is the rigid velocity at the node (up to
+    the re-discretisation's own velocity correction, here below 1 %)."""
+    L = (20, 18, 16)
+    o = oracle.Oracle(*L, **dict(synth.NEMATIC, q0=2 * math.pi / 16), threads=4)
+    o.init_helix(2, 1e-2, 4)
+    a0, X = 3.7, (9.3, 8.6, 7.9)
+    cid = o.add_colloid(X, a0, oracle.PLANAR, 0.02, mobile=True)
+    V = np.array([0.04, -0.03, 0.02])
+    o.set_colloid_velocity(cid, V, (0.0, 0.0, 0.01))
+    c, w = oracle.lattice()
+    c = np.asarray(c, dtype=float)
+    w = np.asarray(w, dtype=float)
+    found = 0
+    for _ in range(30):
+        s0 = o.get_solid()
+        o.step(1)
+        s1 = o.get_solid()
+        unc = np.argwhere((s0 >= 0) & (s1 < 0))
+        if len(unc) == 0:
+            continue
+        Q = o.get_Q()
+        f = o.get_f()
+        col = o.colloid(cid)
+        for z, y, x in unc:
+            nbs = []
+            for dz, dy, dx in ((0, 0, 1), (0, 0, -1), (0, 1, 0), (0, -1, 0), (1, 0, 0), (-1, 0, 0)):
+                zz, yy, xx = (z + dz) % L[2], (y + dy) % L[1], (x + dx) % L[0]
+                if s0[zz, yy, xx] < 0 and s1[zz, yy, xx] < 0:
+                    nbs.append((zz, yy, xx))
+            if not nbs:
+                continue
+            found += 1
+            qm = np.mean([Q[:, n[0], n[1], n[2]] for n in nbs], axis=0)
+            np.testing.assert_allclose(Q[:, z, y, x], qm, rtol=0, atol=1e-15)
+            fn = f[:, z, y, x]
+            rho = fn.sum()
+            rbar = np.mean([f[:, n[0], n[1], n[2]].sum() for n in nbs])
+            assert abs(rho - rbar) < 1e-14
+            u = (fn[:, None] * c).sum(axis=0) / rho
+            cu = c @ u
+            feq = w * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * u @ u)
+            np.testing.assert_allclose(fn, feq, rtol=0, atol=1e-15)
+            d = np.array([x, y, z], dtype=float) - np.asarray(col["X"])
+            d -= np.round(d / np.array(L)) * np.array(L)
+            ub = np.asarray(col["V"]) + np.cross(col["W"], d)
+            assert np.linalg.norm(u - ub) < 1e-2 * np.linalg.norm(ub), (u, ub)
+    assert found >= 3
