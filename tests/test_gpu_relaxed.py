@@ -6,11 +6,12 @@ A 96^3 periodic cholesteric (pitch 32, so that the box holds six Q periods;
 the paper's constants of Sec. 2.1, A0 = 1, K = 0.065, gamma = 3, Gamma = 0.5)
 with one normally anchored colloid of radius 4 (w = 0.01) at the centre is
 relaxed on the GPU in FP32 storage (Q kept as FP32 plus a BF16 remainder)
-until the RMS residual of the Q increment is below 1.6e-8.  With A0 = 1 the
+until the RMS residual of the Q increment is below 2e-8.  With A0 = 1 the
 bulk terms of the molecular field are O(0.3) and cancel at equilibrium, so
-their FP32 evaluation bounds the residual near 1.2-1.4e-8 (measured on
-boxes of 48^3 to 96^3, flat over 500 000 steps); the FP64 oracle then checks
-the state itself:
+their FP32 evaluation bounds the residual at 1.5-1.7e-8 (this geometry:
+2.0e-8 after 150 000 steps, 1.53e-8 after 600 000; the same at 48^3: 1.66e-8),
+and the tolerance sits above that floor; the FP64 oracle then checks the
+state itself:
 
 * it recomputes the free energy F' of that state: within 1e-4 relative;
 * one FP64 step from it has a residual within 20 % of the GPU's last one
@@ -36,7 +37,7 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 PAPER = dict(rho0=1.0, tau=2.5, A0=1.0, gamma=3.0, K=0.065, xi=0.7, Gamma=0.5)
-TOL = 1.6e-8
+TOL = 2e-8
 
 
 def _newton_helix(A0, g, K, q0):
