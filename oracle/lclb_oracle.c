@@ -27,8 +27,11 @@
  *
  * Parity status: every function below is pinned by a CPU test, including the
  * surface value at colloid faces (homeotropic normal at the solid node,
- * planar projection of the largest-eigenvalue director, tie-break) and the
- * LC torque (symmetry and the discrete angular-momentum balance), except the
+ * planar projection of the largest-eigenvalue director, tie-break), the
+ * LC torque (symmetry and the discrete angular-momentum balance), the
+ * uncovered nodes of the re-discretisation (neighbour means, equilibrium),
+ * the moving-surface bounce-back's mass balance and the contact rule
+ * (hand-computed trajectories of node-free colloids), except the
  * drag-anisotropy and cholesteric defect-topology outcomes, which no printed
  * number of the paper fixes (parity unpinned against the paper; the CUDA path
  * is compared with this oracle only).
